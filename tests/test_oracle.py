@@ -1,0 +1,344 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: brute-force
+ranks of every leading submatrix, a second literal reading of Algorithm 1,
+textbook LU, planted rank profiles (Lemma 1), the LEU theorem (Theorem 1),
+hand-derived fixtures, closed-form special cases.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1301_4438_gb300 import workloads as W
+from tests import brute
+from tests.certify import certify
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+PRIMES = [2, 3, 5, 7, 251, 65521, 8388593, 2147483647]
+
+
+def R_from_col(col_of_row, m, n):
+    R = np.zeros((m, n), dtype=np.int64)
+    for i, c in enumerate(col_of_row):
+        if c >= 0:
+            R[i, c] = 1
+    return R
+
+
+def R_from_pq(perm_p, perm_q, r, m, n):
+    R = np.zeros((m, n), dtype=np.int64)
+    R[np.asarray(perm_p[:r]), np.asarray(perm_q[:r])] = 1
+    return R
+
+
+# ---------------------------------------------------------------- field --
+
+def test_is_prime_matches_sieve():
+    N = 5000
+    sieve = np.ones(N, dtype=bool)
+    sieve[:2] = False
+    for i in range(2, int(N ** 0.5) + 1):
+        if sieve[i]:
+            sieve[i * i::i] = False
+    for x in range(N):
+        assert oracle.is_prime(x) == bool(sieve[x]), x
+    for p in PRIMES:
+        assert oracle.is_prime(p)
+    assert not oracle.is_prime(2147483647 * 1 - 2)      # 2^31 - 3 = 5 * 429496729 ... composite
+    assert not oracle.is_prime(65535)
+
+
+def test_rejects_bad_input():
+    A = np.array([[1, 2], [3, 4]], dtype=np.uint32)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.pluq(A, 4)
+    assert e.value.code == -2                       # not prime
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.pluq(A, 3)
+    assert e.value.code == -3                       # entry >= p
+
+
+# ------------------------------------------------- exhaustive tiny cases --
+
+@pytest.mark.parametrize("m,n,p", [(4, 4, 2), (3, 3, 3), (2, 5, 2), (5, 2, 2), (3, 4, 2), (2, 3, 3)])
+def test_rank_profile_exhaustive(m, n, p):
+    """R from incremental row echelon == R from the ranks of all leading submatrices."""
+    As = brute.all_matrices(m, n, p)
+    Rb = brute.rank_profile_matrix(As, p)
+    for b in range(As.shape[0]):
+        col = oracle.rank_profile(As[b].astype(np.uint32), p)
+        assert np.array_equal(R_from_col(col, m, n), Rb[b]), As[b]
+
+
+@pytest.mark.parametrize("m,n,p", [(4, 4, 2), (3, 3, 3), (2, 5, 2), (5, 3, 2), (1, 6, 3), (6, 1, 3)])
+def test_pluq_equals_literal_alg1_exhaustive(m, n, p):
+    """Two independent readings of Algorithm 1 agree bit for bit, and both reveal R."""
+    As = brute.all_matrices(m, n, p)
+    Rb = brute.rank_profile_matrix(As, p)
+    for b in range(As.shape[0]):
+        A = As[b].astype(np.uint32)
+        LU, pp, pq, r = oracle.pluq(A, p)
+        LU1, pp1, pq1, r1 = oracle.pluq_alg1(A, p)
+        assert r == r1
+        assert np.array_equal(pp, pp1) and np.array_equal(pq, pq1), A
+        assert np.array_equal(LU, LU1), A
+        assert np.array_equal(R_from_pq(pp, pq, r, m, n), Rb[b])
+        assert oracle.check_pluq(A, p, LU, pp, pq, r) == 0
+
+
+def test_all_shapes_up_to_4_including_empty():
+    for m in range(0, 5):
+        for n in range(0, 5):
+            if m * n > 12:
+                As = brute.all_matrices(m, n, 2)[::7]
+            elif m * n == 0:
+                As = np.zeros((1, m, n), dtype=np.int64)
+            else:
+                As = brute.all_matrices(m, n, 2)
+            for A in As:
+                A = A.astype(np.uint32)
+                LU, pp, pq, r = oracle.pluq(A, 2)
+                LU1, pp1, pq1, r1 = oracle.pluq_alg1(A, 2)
+                assert (r, pp.tolist(), pq.tolist()) == (r1, pp1.tolist(), pq1.tolist())
+                assert np.array_equal(LU, LU1)
+                assert certify(A, 2, LU, pp, pq, r, exact=True) == ""
+
+
+# --------------------------------------------------------- random small --
+
+def _structured(g, m, n, p):
+    kind = g.integers(0, 5)
+    if kind == 0:                                    # dense uniform
+        return g.integers(0, p, (m, n)).astype(np.uint32)
+    if kind == 1:                                    # sparse
+        A = g.integers(0, p, (m, n)) * (g.random((m, n)) < 0.15)
+        return A.astype(np.uint32)
+    if kind == 2:                                    # low rank planted
+        r = int(g.integers(0, min(m, n) + 1))
+        A, _ = W.planted(m, n, r, p, int(g.integers(1 << 30)))
+        return A
+    if kind == 3:                                    # zero rows / cols, duplicated rows
+        A = g.integers(0, p, (m, n))
+        A[g.random(m) < 0.3, :] = 0
+        A[:, g.random(n) < 0.3] = 0
+        if m > 2:
+            A[m - 1] = A[0]
+        return A.astype(np.uint32)
+    r = int(g.integers(0, min(m, n) + 1))            # rank r product of random factors
+    X = g.integers(0, p, (m, r))
+    Y = g.integers(0, p, (r, n))
+    return brute.matmul_mod(X, Y, p).astype(np.uint32)
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_pluq_equals_literal_alg1_random(p):
+    g = np.random.Generator(np.random.PCG64(p))
+    for _ in range(40):
+        m, n = int(g.integers(1, 41)), int(g.integers(1, 41))
+        A = _structured(g, m, n, p)
+        LU, pp, pq, r = oracle.pluq(A, p)
+        LU1, pp1, pq1, r1 = oracle.pluq_alg1(A, p)
+        assert r == r1
+        assert np.array_equal(pp, pp1) and np.array_equal(pq, pq1)
+        assert np.array_equal(LU, LU1)
+        assert certify(A, p, LU, pp, pq, r, exact=True) == ""
+
+
+@pytest.mark.parametrize("p", [2, 5, 65521])
+def test_leading_submatrix_rank_profiles(p):
+    """Corollary of Lemma 2: rank profiles of every leading (k,t) submatrix are read off R."""
+    g = np.random.Generator(np.random.PCG64(1000 + p))
+    for _ in range(6):
+        m, n = int(g.integers(2, 9)), int(g.integers(2, 9))
+        A = _structured(g, m, n, p)
+        LU, pp, pq, r = oracle.pluq(A, p)
+        R = R_from_pq(pp, pq, r, m, n)
+        for k in range(1, m + 1):
+            for t in range(1, n + 1):
+                sub = A[:k, :t].astype(np.int64)
+                # row rank profile of the leading block, greedily by rank tests
+                rows, cols = [], []
+                for i in range(k):
+                    if brute.batch_rank(sub[rows + [i]][None], p)[0] > len(rows):
+                        rows.append(i)
+                for j in range(t):
+                    if brute.batch_rank(sub[:, cols + [j]][None], p)[0] > len(cols):
+                        cols.append(j)
+                Rk = R[:k, :t]
+                assert rows == sorted(np.nonzero(Rk.any(axis=1))[0].tolist())
+                assert cols == sorted(np.nonzero(Rk.any(axis=0))[0].tolist())
+
+
+def test_leu_theorem_random():
+    """Theorem 1: P [L 0; M Y] P^T unit lower and Q^T [U V; 0 Z] Q upper."""
+    g = np.random.Generator(np.random.PCG64(77))
+    for _ in range(60):
+        p = int(g.choice(PRIMES))
+        m, n = int(g.integers(1, 30)), int(g.integers(1, 30))
+        A = _structured(g, m, n, p)
+        LU, pp, pq, r = oracle.pluq(A, p)
+        Lfull = np.zeros((m, m), dtype=np.int64)
+        Lfull[:, :r] = np.tril(LU[:, :r].astype(np.int64), -1)
+        Y = np.tril(g.integers(0, p, (m - r, m - r)), -1)
+        Lfull[r:, r:] = Y
+        np.fill_diagonal(Lfull, 1)
+        Pm = np.zeros((m, m), dtype=np.int64)
+        Pm[pp, np.arange(m)] = 1
+        Lbar = Pm @ Lfull @ Pm.T
+        assert np.array_equal(Lbar, np.tril(Lbar)) and np.all(np.diagonal(Lbar) == 1)
+        for Zkind in ("I", "upper", "zero"):
+            Ufull = np.zeros((n, n), dtype=np.int64)
+            Ufull[:r, :] = np.triu(LU[:r, :].astype(np.int64))
+            if Zkind == "I":
+                Ufull[r:, r:] = np.eye(n - r, dtype=np.int64)
+            elif Zkind == "upper":
+                Ufull[r:, r:] = np.triu(g.integers(0, p, (n - r, n - r)))
+            Qm = np.zeros((n, n), dtype=np.int64)
+            Qm[np.arange(n), pq] = 1
+            Ubar = Qm.T @ Ufull @ Qm
+            assert np.array_equal(Ubar, np.triu(Ubar))
+
+
+# ------------------------------------------------------- planted / sizes --
+
+@pytest.mark.parametrize("m,n,r,p", [(50, 60, 20, 65521), (64, 64, 64, 8388593),
+                                      (100, 37, 30, 2147483647), (200, 200, 100, 251),
+                                      (40, 90, 0, 7), (33, 17, 17, 2)])
+def test_planted_rank_profile_recovered(m, n, r, p):
+    A, pl = W.planted(m, n, r, p, seed=m * 1000 + n + r)
+    col = oracle.rank_profile(A, p)
+    assert np.array_equal(col, pl.rank_profile())
+    LU, pp, pq, rr = oracle.pluq(A, p)
+    assert rr == r
+    assert certify(A, p, LU, pp, pq, rr, exact=True, expected_col_of_row=pl.rank_profile()) == ""
+
+
+def test_planted_config_256():
+    cfg = W.CONFIGS["planted_256"]
+    A, pl = W.make(cfg)
+    LU, pp, pq, r = oracle.pluq(A, cfg.p)
+    assert r == 200
+    assert certify(A, cfg.p, LU, pp, pq, r, exact=True, expected_col_of_row=pl.rank_profile()) == ""
+
+
+def test_generator_entries_exact():
+    """Sampled entries of A = L0[:,rows] U0[cols,:] recomputed with Python integers."""
+    for (m, n, r, p) in [(60, 70, 25, 2147483647), (40, 40, 40, 8388593)]:
+        A, pl = W.planted(m, n, r, p, seed=5)
+        g = np.random.Generator(np.random.PCG64(9))
+        for _ in range(50):
+            i, j = int(g.integers(m)), int(g.integers(n))
+            v = sum(int(pl.Lc[i, t]) * int(pl.Ur[t, j]) for t in range(r)) % p
+            assert int(A[i, j]) == v
+
+
+# ------------------------------------------------- special closed forms --
+
+@pytest.mark.parametrize("n,p", [(8, 65521), (17, 2147483647), (24, 251)])
+def test_generic_rank_profile_is_plain_lu(n, p):
+    """All leading principal minors nonzero => P = Q = I and L, U = LU without pivoting."""
+    g = np.random.Generator(np.random.PCG64(n))
+    while True:
+        A = g.integers(0, p, (n, n)).astype(np.uint32)
+        lu = brute.doolittle(A, p)
+        if lu is not None:
+            break
+    L, U = lu
+    LU, pp, pq, r = oracle.pluq(A, p)
+    assert r == n
+    assert np.array_equal(pp, np.arange(n)) and np.array_equal(pq, np.arange(n))
+    assert np.array_equal(np.tril(LU.astype(np.int64), -1), np.tril(L, -1))
+    assert np.array_equal(np.triu(LU.astype(np.int64)), U)
+
+
+@pytest.mark.parametrize("m,n", [(0, 0), (0, 5), (5, 0), (7, 9), (1, 1)])
+def test_zero_matrix(m, n):
+    A = np.zeros((m, n), dtype=np.uint32)
+    LU, pp, pq, r = oracle.pluq(A, 65521)
+    assert r == 0
+    assert np.array_equal(pp, np.arange(m)) and np.array_equal(pq, np.arange(n))
+    assert not LU.any()
+
+
+def test_scaled_partial_permutation():
+    """R of a scaled partial permutation matrix is its support; L = I and U = diag."""
+    g = np.random.Generator(np.random.PCG64(3))
+    p = 65521
+    for _ in range(20):
+        m, n = int(g.integers(1, 40)), int(g.integers(1, 40))
+        r = int(g.integers(0, min(m, n) + 1))
+        rows = g.choice(m, r, replace=False)
+        cols = g.choice(n, r, replace=False)
+        vals = g.integers(1, p, r)
+        A = np.zeros((m, n), dtype=np.uint32)
+        A[rows, cols] = vals
+        LU, pp, pq, rr = oracle.pluq(A, p)
+        assert rr == r
+        assert np.array_equal(R_from_pq(pp, pq, r, m, n), (A != 0).astype(np.int64))
+        expect = np.zeros((m, n), dtype=np.uint32)
+        expect[np.arange(r), np.arange(r)] = A[pp[:r], pq[:r]]
+        assert np.array_equal(LU, expect)
+
+
+# ------------------------------------------------------ golden fixtures --
+
+def _load_golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def test_golden_rotation_base_case():
+    """A 2 x 6 case where a transposition in the m = 1 base case would report the
+    column rank profile {1, 2}; the rank definition gives {0, 2}."""
+    gd = _load_golden("rotation_2x6.json")
+    A = np.array(gd["A"], dtype=np.uint32)
+    p = gd["p"]
+    for f in (oracle.pluq, oracle.pluq_alg1):
+        LU, pp, pq, r = f(A, p)
+        assert r == gd["rank"]
+        assert sorted(pq[:r].tolist()) == gd["col_rank_profile"]
+        assert sorted(pp[:r].tolist()) == gd["row_rank_profile"]
+        assert [[int(a), int(b)] for a, b in zip(pp[:r], pq[:r])] == gd["pivots_in_order"]
+
+
+def test_golden_alg1_order_8x8():
+    """A case where Algorithm 2's growing leading submatrix would meet pivot (3,4)
+    before (2,6); Algorithm 1 (and the canonical order) put (2,6) first."""
+    gd = _load_golden("alg1_order_8x8.json")
+    A = np.array(gd["A"], dtype=np.uint32)
+    p = gd["p"]
+    for f in (oracle.pluq, oracle.pluq_alg1):
+        LU, pp, pq, r = f(A, p)
+        assert [[int(a), int(b)] for a, b in zip(pp[:r], pq[:r])] == gd["pivots_in_order"]
+
+
+# ------------------------------------------------ BLAS-like subroutines --
+
+def test_matmul_sub_against_python_integers():
+    g = np.random.Generator(np.random.PCG64(11))
+    for p in (2, 65521, 2147483647):
+        for (M, N, K) in [(5, 7, 3), (16, 9, 33), (1, 1, 1), (4, 6, 0)]:
+            A = g.integers(0, p, (M, K)).astype(np.uint32)
+            B = g.integers(0, p, (K, N)).astype(np.uint32)
+            C = g.integers(0, p, (M, N)).astype(np.uint32)
+            got = oracle.matmul_sub(C, A, B, p)
+            want = (C.astype(object) - brute.matmul_mod(A, B, p).astype(object)) % p
+            assert np.array_equal(got.astype(np.int64), want.astype(np.int64))
+
+
+def test_trsm_solves():
+    g = np.random.Generator(np.random.PCG64(12))
+    for p in (3, 65521, 2147483647):
+        for (r, N) in [(1, 5), (7, 3), (20, 20)]:
+            L = np.tril(g.integers(0, p, (r, r)), -1)
+            Lu = L + np.eye(r, dtype=np.int64)
+            B = g.integers(0, p, (r, N)).astype(np.uint32)
+            X = oracle.trsm_left_lower_unit((L + 5 * np.eye(r, dtype=np.int64)) % p, B, p)
+            assert np.array_equal(brute.matmul_mod(Lu, X, p), B.astype(np.int64))
+            U = np.triu(g.integers(1, p, (r, r)))
+            B2 = g.integers(0, p, (N, r)).astype(np.uint32)
+            X2 = oracle.trsm_right_upper(U, B2, p)
+            assert np.array_equal(brute.matmul_mod(X2, U, p), B2.astype(np.int64))
