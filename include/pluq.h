@@ -1,0 +1,172 @@
+/*
+ * libpluq — rank-profile-revealing PLUQ decomposition over Z/pZ on one GB300.
+ *
+ * The method is Algorithm 1 of Dumas, Pernet & Sultan, "Simultaneous
+ * computation of the row and column rank profiles" (arXiv 1301.4438): a
+ * quad-recursive elimination whose permutations P and Q reveal the row and
+ * column rank profiles of the matrix and of each of its leading submatrices.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Field: Z/pZ with p prime, 2 <= p < 2^31.  Elements are uint32 in [0, p).
+ *    Every result is exact (bit-identical to textbook arithmetic mod p).
+ *  - Matrices: row-major uint32 with a row stride (ld >= number of columns).
+ *  - Pointers named d_* are DEVICE pointers (cudaMalloc'd or torch-owned),
+ *    h_* are HOST pointers.  The caller owns every buffer; the library keeps no
+ *    pointer after a call returns and allocates no device memory of its own:
+ *    scratch comes from the caller's workspace (see pluq_workspace_size).
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Return value: a pluq_status.  Argument errors are reported before any
+ *    work is queued and leave every buffer untouched.
+ *
+ * Permutation vectors (Algorithm 1 output, Sec. 2)
+ * ------------------------------------------------
+ *  perm_p[i] = original row index placed at packed row i   (P[perm_p[i], i] = 1)
+ *  perm_q[j] = original column index placed at packed column j (Q[j, perm_q[j]] = 1)
+ *  so that A[perm_p[i]][perm_q[j]] = ([L; M] [U V])[i][j].  The first r entries
+ *  are the pivots in the order Algorithm 1 finds them; the remaining rows and
+ *  columns follow in increasing order.
+ */
+#ifndef PLUQ_H
+#define PLUQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLUQ_OK = 0,
+    PLUQ_EINVAL = -1,       /* bad size, stride, null pointer or flag */
+    PLUQ_ENOTPRIME = -2,    /* p is not a prime in [2, 2^31) */
+    PLUQ_ERANGE = -3,       /* an input entry is >= p (no silent reduction) */
+    PLUQ_ENOMEM = -4,       /* workspace smaller than pluq_workspace_size() */
+    PLUQ_ECUDA = -5,        /* a CUDA runtime call failed */
+    PLUQ_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
+    PLUQ_EINTERNAL = -7,    /* an internal consistency check failed */
+    PLUQ_EUNSUPPORTED = -8  /* the requested kernel form is not available */
+} pluq_status;
+
+/* Kernel used for the modular matrix products (MM) inside the factorisation. */
+typedef enum {
+    PLUQ_MM_AUTO = 0,       /* the tensor-core form */
+    PLUQ_MM_SIMT = 1,       /* plain CUDA-core form: 32x32->64-bit products */
+    PLUQ_MM_TENSOR = 2      /* 8-bit limbs on tcgen05 tensor cores (bf16 x bf16 -> fp32,
+                               exact below 2^24), mod-p reduction in the epilogue */
+} pluq_mm_kind;
+
+/* Human-readable text of a status code (static storage). */
+const char *pluq_status_string(int status);
+
+/*
+ * Bytes of device workspace pluq_mod_p needs for an m x n matrix mod p.
+ * Writes the size to *h_bytes.  Depends only on (m, n, p).
+ */
+pluq_status pluq_workspace_size(int64_t m, int64_t n, uint32_t p, size_t *h_bytes);
+
+/*
+ * PLUQ decomposition, Algorithm 1 (Sec. 2), in place.
+ *   d_A      m x n, stride lda >= n, entries in [0, p).  On return it holds the
+ *            packed form [L\U V; M 0] of the Algorithm 1 output contract: L unit
+ *            lower r x r (diagonal not stored), U upper r x r, V r x (n-r),
+ *            M (m-r) x r, and a zero (m-r) x (n-r) block.
+ *   d_perm_p m int32, d_perm_q n int32 (see the convention above).
+ *   h_rank   receives r.
+ *   d_work   workspace of ws_bytes >= pluq_workspace_size(m, n, p) bytes.
+ *   mm_kind  a pluq_mm_kind.
+ * Zero dimensions are allowed (Sec. 2): r = 0 and identity permutations.
+ * The ranks of sub-blocks decide the shapes of later steps, so the call
+ * returns only after the factorisation has completed on `stream`.
+ * Errors: EINVAL, ENOTPRIME, ERANGE (checked on the device before any write),
+ * ENOMEM, ECUDA, EUNSUPPORTED.
+ */
+pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                       int32_t *d_perm_p, int32_t *d_perm_q, int64_t *h_rank,
+                       void *d_work, size_t ws_bytes, int mm_kind, void *stream);
+
+/*
+ * Row rank profile of A (Corollary of Lemma 2, Sec. 4): the sorted first r
+ * entries of perm_p.  d_out receives r int32.  Asynchronous on `stream`.
+ */
+pluq_status row_rank_profile(const int32_t *d_perm_p, int64_t m, int64_t r,
+                             int32_t *d_out, void *stream);
+
+/* Column rank profile of A: the sorted first r entries of perm_q. */
+pluq_status col_rank_profile(const int32_t *d_perm_q, int64_t n, int64_t r,
+                             int32_t *d_out, void *stream);
+
+/*
+ * Rank profile matrix R = P diag(I_r, 0) Q (Lemma 2, Sec. 4) as its r ones:
+ * R[d_rows[t], d_cols[t]] = 1, sorted by row.  The rank profiles of any leading
+ * k x t submatrix of A are the rows / columns of the ones in [0,k) x [0,t).
+ */
+pluq_status rank_profile_matrix(const int32_t *d_perm_p, const int32_t *d_perm_q,
+                                int64_t m, int64_t n, int64_t r,
+                                int32_t *d_rows, int32_t *d_cols, void *stream);
+
+/*
+ * Hot-path kernels of Algorithm 1, callable on their own.
+ *
+ * MM(C, A, B) of Sec. 2: C <- C - A B mod p (or C <- A B mod p when `assign`
+ * is nonzero), A M x K, B K x N, C M x N.  C must not overlap A or B in the
+ * SIMT form; the tensor form first splits A and B into limb planes held in
+ * the workspace, so C may overlap B there.  Asynchronous on `stream`.
+ * Workspace: pluq_modmm_workspace_size.
+ */
+pluq_status pluq_modmm_workspace_size(int64_t M, int64_t N, int64_t K, uint32_t p,
+                                      int mm_kind, size_t *h_bytes);
+pluq_status pluq_modmm(uint32_t *d_C, int64_t ldc, const uint32_t *d_A, int64_t lda,
+                       const uint32_t *d_B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                       uint32_t p, int assign, int mm_kind, void *d_work, size_t ws_bytes,
+                       void *stream);
+
+/*
+ * TRSM of Sec. 2.  Left: B <- L^{-1} B, L r x r unit lower (diagonal not
+ * read), B r x N.  Right: B <- B U^{-1}, U r x r upper with nonzero diagonal,
+ * B M x r.  Computed as the triangular inverse (recursive block formula) times
+ * B on the modular MM kernels.  Asynchronous on `stream`.  Workspace:
+ * pluq_trsm_workspace_size.
+ */
+pluq_status pluq_trsm_workspace_size(int64_t r, int64_t other, uint32_t p, int mm_kind,
+                                     size_t *h_bytes);
+pluq_status pluq_trsm_left_lower_unit(const uint32_t *d_L, int64_t ldl, uint32_t *d_B,
+                                      int64_t ldb, int64_t r, int64_t N, uint32_t p,
+                                      int mm_kind, void *d_work, size_t ws_bytes,
+                                      void *stream);
+pluq_status pluq_trsm_right_upper(const uint32_t *d_U, int64_t ldu, uint32_t *d_B,
+                                  int64_t ldb, int64_t M, int64_t r, uint32_t p,
+                                  int mm_kind, void *d_work, size_t ws_bytes, void *stream);
+
+/*
+ * PermR / PermC of Sec. 2 on a block: rows (cols) [0, count) of the block at
+ * d_X are replaced by rows (cols) d_perm[0..count) of it; the block is
+ * count x width (width x count).  Uses count*width*4 bytes of d_work.
+ */
+pluq_status pluq_perm_rows(uint32_t *d_X, int64_t ldx, int64_t count, int64_t width,
+                           const int32_t *d_perm, void *d_work, size_t ws_bytes,
+                           void *stream);
+pluq_status pluq_perm_cols(uint32_t *d_X, int64_t ldx, int64_t height, int64_t count,
+                           const int32_t *d_perm, void *d_work, size_t ws_bytes,
+                           void *stream);
+
+/*
+ * Base case of the recursion (Algorithm 1 on a block of at most
+ * pluq_leaf_max_rows() x pluq_leaf_max_cols()): one thread block finds the
+ * block's rank profile matrix by row-echelon elimination, orders its ones as
+ * Algorithm 1 would, and eliminates without pivoting in that order.  Same
+ * in-place contract as pluq_mod_p; d_rank receives r (device int32).
+ */
+int64_t pluq_leaf_max_rows(void);
+int64_t pluq_leaf_max_cols(void);
+pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                      int32_t *d_perm_p, int32_t *d_perm_q, int32_t *d_rank, void *stream);
+
+/* Number of 8-bit limbs the tensor form splits residues mod p into (1 to 4). */
+int pluq_tensor_limbs(uint32_t p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLUQ_H */

@@ -1,0 +1,189 @@
+// Shared device/host helpers of libpluq: modular arithmetic over Z/pZ
+// (p < 2^31), error plumbing, launch helpers.  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/pluq.h"
+
+namespace pluq {
+
+// ----------------------------------------------------------------- field --
+// Residues live in [0, p).  Products of two residues are < 2^62.
+//
+// Barrett reduction of x < 2^64 with mu = floor((2^64 - 1) / p): the quotient
+// estimate q = hi64(x * mu) satisfies floor(x/p) - 1 <= q <= floor(x/p), so
+// x - q p lies in [0, 2p) and one conditional subtraction finishes it.
+struct Field {
+    uint32_t p;
+    uint64_t mu;
+};
+
+inline Field make_field(uint32_t p)
+{
+    Field f;
+    f.p = p;
+    f.mu = ~0ull / p;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t reduce64(uint64_t x, const Field &F)
+{
+    uint64_t q = __umul64hi(x, F.mu);
+    uint64_t r = x - q * (uint64_t)F.p;
+    return (uint32_t)(r >= F.p ? r - F.p : r);
+}
+
+__device__ __forceinline__ uint32_t mul_mod(uint32_t a, uint32_t b, const Field &F)
+{
+    return reduce64((uint64_t)a * b, F);
+}
+
+__device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t p)
+{
+    uint32_t s = a + b;            // < 2^32 since a, b < 2^31
+    return s >= p ? s - p : s;
+}
+
+__device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t p)
+{
+    return a >= b ? a - b : a + (p - b);
+}
+
+// (a*b - c*d) mod p with one reduction: a*b + c*(p-d) < 2^63.
+__device__ __forceinline__ uint32_t mul_sub_mul_mod(uint32_t a, uint32_t b, uint32_t c,
+                                                    uint32_t d, const Field &F)
+{
+    uint64_t x = (uint64_t)a * b + (uint64_t)c * (d == 0 ? 0u : F.p - d);
+    return reduce64(x, F);
+}
+
+// Inverse of a nonzero residue by the extended Euclidean algorithm.
+__device__ __forceinline__ uint32_t inv_mod(uint32_t a, uint32_t p)
+{
+    uint32_t r0 = p, r1 = a;
+    int64_t s0 = 0, s1 = 1;
+    while (r1 != 0) {
+        uint32_t q = r0 / r1;
+        uint32_t t = r0 - q * r1;
+        r0 = r1;
+        r1 = t;
+        int64_t u = s0 - (int64_t)q * s1;
+        s0 = s1;
+        s1 = u;
+    }
+    int64_t v = s0 % (int64_t)p;
+    if (v < 0) v += p;
+    return (uint32_t)v;
+}
+
+// --------------------------------------------------------------- limbs --
+// Balanced base-256 digits of the centred representative c of x
+// (c = x or x - p, |c| <= p/2): c = sum_l d_l 256^l with d_l in [-128, 127]
+// for l < L-1 and |d_{L-1}| <= 128.  Every digit is an integer of magnitude
+// <= 128, exact in bf16, and a digit product is at most 2^14 in magnitude.
+inline int limbs_for_prime(uint32_t p)
+{
+    // smallest L with (p-1)/2 <= 128 (256^L - 1) / 255
+    uint64_t half = (uint64_t)(p - 1) / 2;
+    uint64_t cap = 128;      // 128 (256^1 - 1)/255
+    int L = 1;
+    while (half > cap) {
+        cap = cap * 256 + 128;
+        ++L;
+    }
+    return L;
+}
+
+// ---------------------------------------------------------------- misc --
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, off = 0;
+    void *take(size_t bytes, size_t align = 256)
+    {
+        size_t o = align_up(off, align);
+        if (o + bytes > size) return nullptr;
+        off = o + bytes;
+        return base + o;
+    }
+};
+
+#define PLUQ_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return PLUQ_ECUDA;             \
+    } while (0)
+
+#define PLUQ_TRY(expr)                                        \
+    do {                                                      \
+        pluq_status _s = (expr);                              \
+        if (_s != PLUQ_OK) return _s;                         \
+    } while (0)
+
+inline pluq_status last_launch()
+{
+    return cudaGetLastError() == cudaSuccess ? PLUQ_OK : PLUQ_ECUDA;
+}
+
+// --------------------------------------------------- internal launchers --
+// Strided block descriptor: element (i, j) at ptr[i*ld + j].
+struct Blk {
+    uint32_t *ptr;
+    int64_t ld;
+};
+
+enum MMMode { MM_SUB = 0, MM_ASSIGN = 1, MM_NEG_ASSIGN = 2 };
+
+// Modular product on a batch of equally shaped problems:
+//   C_b <- C_b - A_b B_b | A_b B_b | -A_b B_b (mode), b < batch, with
+//   X_b = X + b * stride_X.  SIMT form.
+pluq_status launch_mm_simt(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B,
+                           int64_t ldb, int64_t M, int64_t N, int64_t K, Field F, int mode,
+                           int64_t batch, int64_t sA, int64_t sB, int64_t sC,
+                           cudaStream_t st);
+
+// Tensor-core form; scratch for limb planes comes from the arena.
+pluq_status launch_mm_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B,
+                         int64_t ldb, int64_t M, int64_t N, int64_t K, Field F, int mode,
+                         int64_t batch, int64_t sA, int64_t sB, int64_t sC, Arena &ar,
+                         cudaStream_t st);
+size_t mm_tc_workspace(int64_t M, int64_t N, int64_t K, uint32_t p, int64_t batch);
+
+// Dispatch on the kind (SIMT needs C disjoint from A and B).
+pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uint32_t *B,
+                      int64_t ldb, int64_t M, int64_t N, int64_t K, Field F, int mode,
+                      int64_t batch, int64_t sA, int64_t sB, int64_t sC, Arena &ar,
+                      cudaStream_t st);
+
+// Row/column gathers: dst[i][j] = src[rmap(i)][cmap(j)], maps optional.
+pluq_status launch_gather(Blk dst, const uint32_t *src, int64_t lds, int64_t rows,
+                          int64_t cols, const int32_t *rmap, const int32_t *cmap,
+                          cudaStream_t st);
+pluq_status launch_copy(Blk dst, const uint32_t *src, int64_t lds, int64_t rows,
+                        int64_t cols, cudaStream_t st);
+pluq_status launch_zero(Blk dst, int64_t rows, int64_t cols, cudaStream_t st);
+
+// Triangular inverses into X (r x r, ld ldx), and the TRSMs built on them.
+pluq_status tri_inv_lower_unit(const uint32_t *L, int64_t ldl, Blk X, int64_t r, Field F,
+                               int kind, Arena &ar, cudaStream_t st);
+pluq_status tri_inv_upper(const uint32_t *U, int64_t ldu, Blk X, int64_t r, Field F,
+                          int kind, Arena &ar, cudaStream_t st);
+pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t r, int64_t N,
+                                 Field F, int kind, Arena &ar, cudaStream_t st);
+pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, int64_t r,
+                             Field F, int kind, Arena &ar, cudaStream_t st);
+size_t trsm_workspace(int64_t r, int64_t other, uint32_t p, int kind);
+
+pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st);
+
+// Leaf (base case) of the recursion.
+constexpr int LEAF_MAX = 128;
+pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
+                        int32_t *perm_p, int32_t *perm_q, int32_t *rank, cudaStream_t st);
+
+}  // namespace pluq

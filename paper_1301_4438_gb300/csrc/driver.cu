@@ -1,0 +1,426 @@
+// Algorithm 1 (Sec. 2) driven from the host, every step a kernel on the
+// caller's stream, and the C-ABI entry points of include/pluq.h.
+//
+// The ranks r1..r4 of the four recursive calls decide the shapes of the next
+// steps, so the host reads each leaf's rank back (pinned host word) before it
+// continues; everything else is queued asynchronously.  Blocks are addressed
+// in place inside the caller's matrix (pointer + row stride); permutations of
+// a block go through a scratch copy.
+#include <mutex>
+#include <new>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace pluq {
+
+pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st);
+pluq_status launch_compose(const int32_t *p1, const int32_t *p2, const int32_t *p3,
+                           const int32_t *p4, const int32_t *q1, const int32_t *q2,
+                           const int32_t *q3, const int32_t *q4, int32_t *p, int32_t *q,
+                           int32_t *smap, int32_t *tmap, int64_t m, int64_t n, int64_t k,
+                           int64_t h, int64_t r1, int64_t r2, int64_t r3, int64_t r4,
+                           cudaStream_t st);
+pluq_status launch_rank_sort(const int32_t *key, const int32_t *val, int64_t r, int32_t *out_key,
+                             int32_t *out_val, cudaStream_t st);
+pluq_status launch_check_range(const uint32_t *A, int64_t lda, int64_t m, int64_t n, uint32_t p,
+                               int32_t *flag, cudaStream_t st);
+
+pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uint32_t *B,
+                      int64_t ldb, int64_t M, int64_t N, int64_t K, Field F, int mode,
+                      int64_t batch, int64_t sA, int64_t sB, int64_t sC, Arena &ar,
+                      cudaStream_t st)
+{
+    if (kind == PLUQ_MM_SIMT)
+        return launch_mm_simt(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, st);
+    return launch_mm_tc(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, ar, st);
+}
+
+namespace {
+
+bool is_prime_u32(uint32_t p)
+{
+    if (p < 2) return false;
+    for (uint64_t d = 2; d * d <= p; ++d)
+        if (p % d == 0) return false;
+    return true;
+}
+
+// Pinned host word for rank read-back (one per host thread).
+int32_t *pinned_word()
+{
+    thread_local int32_t *w = nullptr;
+    if (!w) {
+        if (cudaHostAlloc((void **)&w, 64, cudaHostAllocDefault) != cudaSuccess) w = nullptr;
+    }
+    return w;
+}
+
+struct Ctx {
+    Field F;
+    int kind;
+    cudaStream_t st;
+    Arena ar;             // scratch for products / TRSM (stack discipline)
+    uint32_t *gather;     // m*n scratch for permutations
+    uint32_t *icopy;      // copy of I (r3 x r2)
+    int32_t *smap, *tmap; // S and T index maps of the current node
+    int32_t *vstack;      // child permutation vectors (stack discipline)
+    size_t vtop, vcap;
+    int32_t *d_rank;
+    int32_t *h_rank;
+    int64_t leaves = 0;
+};
+
+int32_t *vtake(Ctx &c, int64_t len)
+{
+    size_t need = (size_t)(len > 0 ? len : 1);
+    need = align_up(need, 64);
+    if (c.vtop + need > c.vcap) return nullptr;
+    int32_t *v = c.vstack + c.vtop;
+    c.vtop += need;
+    return v;
+}
+
+// rows [0, rows) x cols [0, cols) of the block X <- gathered with maps (in place
+// through the scratch copy)
+pluq_status permute_block(Ctx &c, uint32_t *X, int64_t ldx, int64_t rows, int64_t cols,
+                          const int32_t *rmap, const int32_t *cmap)
+{
+    if (rows <= 0 || cols <= 0 || (!rmap && !cmap)) return PLUQ_OK;
+    PLUQ_TRY(launch_gather(Blk{c.gather, cols}, X, ldx, rows, cols, rmap, cmap, c.st));
+    return launch_copy(Blk{X, ldx}, c.gather, cols, rows, cols, c.st);
+}
+
+pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t *pp,
+                int32_t *pq, int64_t &r)
+{
+    r = 0;
+    if (m == 0 || n == 0) {
+        PLUQ_TRY(launch_iota(pp, m, c.st));
+        PLUQ_TRY(launch_iota(pq, n, c.st));
+        return PLUQ_OK;
+    }
+    if (m <= LEAF_MAX && n <= LEAF_MAX) {
+        PLUQ_TRY(launch_leaf(A, m, n, lda, c.F, pp, pq, c.d_rank, c.st));
+        PLUQ_CUDA_TRY(cudaMemcpyAsync(c.h_rank, c.d_rank, sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, c.st));
+        PLUQ_CUDA_TRY(cudaStreamSynchronize(c.st));
+        r = *c.h_rank;
+        ++c.leaves;
+        if (r < 0 || r > m || r > n) return PLUQ_EINTERNAL;
+        return PLUQ_OK;
+    }
+    const int64_t k = m / 2, h = n / 2;
+    const size_t vmark = c.vtop;
+    int32_t *p1 = vtake(c, k), *q1 = vtake(c, h), *p2 = vtake(c, k), *q2 = vtake(c, n - h);
+    int32_t *p3 = vtake(c, m - k), *q3 = vtake(c, h), *p4 = vtake(c, m - k), *q4 = vtake(c, n - h);
+    if (!q4) return PLUQ_ENOMEM;
+    const Field F = c.F;
+    auto at = [&](int64_t i, int64_t j) { return A + i * lda + j; };
+
+    // A1 = P1 [L1;M1][U1 V1] Q1
+    int64_t r1;
+    PLUQ_TRY(rec(c, A, k, h, lda, p1, q1, r1));
+    // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
+    PLUQ_TRY(permute_block(c, at(0, h), lda, k, n - h, p1, nullptr));
+    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, h, nullptr, q1));
+    // D <- L1^{-1} B1 ; E <- C1 U1^{-1}
+    PLUQ_TRY(trsm_left_lower_unit(A, lda, Blk{at(0, h), lda}, r1, n - h, F, c.kind, c.ar, c.st));
+    PLUQ_TRY(trsm_right_upper(A, lda, Blk{at(k, 0), lda}, m - k, r1, F, c.kind, c.ar, c.st));
+    // [F;H] <- [B2;A4] - [M1;E] D ; G <- C2 - E V1
+    PLUQ_TRY(launch_mm(c.kind, Blk{at(r1, h), lda}, at(r1, 0), lda, at(0, h), lda, m - r1, n - h,
+                       r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+    PLUQ_TRY(launch_mm(c.kind, Blk{at(k, r1), lda}, at(k, 0), lda, at(0, r1), lda, m - k, h - r1,
+                       r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+    // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
+    int64_t r2, r3;
+    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, r2));
+    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, r3));
+    // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
+    PLUQ_TRY(permute_block(c, at(k, h), lda, m - k, n - h, p3, q2));
+    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, r1, p3, nullptr));
+    PLUQ_TRY(permute_block(c, at(r1, 0), lda, k - r1, r1, p2, nullptr));
+    PLUQ_TRY(permute_block(c, at(0, h), lda, r1, n - h, nullptr, q2));
+    PLUQ_TRY(permute_block(c, at(0, r1), lda, r1, h - r1, nullptr, q3));
+    // [I;K] <- [H1;H3] U2^{-1}
+    const uint32_t *U2 = at(r1, h);
+    PLUQ_TRY(trsm_right_upper(U2, lda, Blk{at(k, h), lda}, m - k, r2, F, c.kind, c.ar, c.st));
+    // keep I; [J N] <- L3^{-1} [I H2]
+    if (r3 > 0 && r2 > 0) PLUQ_TRY(launch_copy(Blk{c.icopy, r2}, at(k, h), lda, r3, r2, c.st));
+    const uint32_t *L3 = at(k, r1);
+    PLUQ_TRY(trsm_left_lower_unit(L3, lda, Blk{at(k, h), lda}, r3, n - h, F, c.kind, c.ar, c.st));
+    // O <- N - J V2
+    PLUQ_TRY(launch_mm(c.kind, Blk{at(k, h + r2), lda}, at(k, h), lda, at(r1, h + r2), lda, r3,
+                       n - h - r2, r2, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+    if (r3 > 0 && r2 > 0) PLUQ_TRY(launch_copy(Blk{at(k, h), lda}, c.icopy, r2, r3, r2, c.st));
+    // R <- H4 - K V2 - M3 O
+    PLUQ_TRY(launch_mm(c.kind, Blk{at(k + r3, h + r2), lda}, at(k + r3, h), lda, at(r1, h + r2),
+                       lda, m - k - r3, n - h - r2, r2, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+    PLUQ_TRY(launch_mm(c.kind, Blk{at(k + r3, h + r2), lda}, at(k + r3, r1), lda, at(k, h + r2),
+                       lda, m - k - r3, n - h - r2, r3, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+    // R = P4 [L4;M4][U4 V4] Q4
+    int64_t r4;
+    PLUQ_TRY(rec(c, at(k + r3, h + r2), m - k - r3, n - h - r2, lda, p4, q4, r4));
+    // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T
+    PLUQ_TRY(permute_block(c, at(k + r3, 0), lda, m - k - r3, h + r2, p4, nullptr));
+    PLUQ_TRY(permute_block(c, at(0, h + r2), lda, k + r3, n - h - r2, nullptr, q4));
+    // P, Q and the block permutations S, T ; A <- S^T A T^T
+    PLUQ_TRY(launch_compose(p1, p2, p3, p4, q1, q2, q3, q4, pp, pq, c.smap, c.tmap, m, n, k, h,
+                            r1, r2, r3, r4, c.st));
+    PLUQ_TRY(permute_block(c, A, lda, m, n, c.smap, c.tmap));
+    r = r1 + r2 + r3 + r4;
+    c.vtop = vmark;
+    return PLUQ_OK;
+}
+
+struct Layout {
+    size_t gather, icopy, maps, vstack, small, arena, total;
+};
+
+Layout layout(int64_t m, int64_t n, uint32_t p, int kind)
+{
+    Layout L{};
+    const int64_t mn = m < n ? m : n;
+    L.gather = align_up((size_t)m * n * 4 + 256, 256);
+    L.icopy = align_up((size_t)((m + 1) / 2) * ((n + 1) / 2) * 4 + 256, 256);
+    L.maps = align_up((size_t)(m + n + 2) * 4, 256);
+    L.vstack = align_up((size_t)(8 * (m + n) + 64 * 64) * 4, 256);
+    L.small = 256;
+    L.arena = trsm_workspace(mn, m > n ? m : n, p, kind);
+    if (kind != PLUQ_MM_SIMT) L.arena += mm_tc_workspace(m, n, mn, p, 1);
+    L.arena = align_up(L.arena + (1 << 20), 256);
+    L.total = L.gather + L.icopy + L.maps + L.vstack + L.small + L.arena;
+    return L;
+}
+
+int resolve_kind(int kind)
+{
+    if (kind == PLUQ_MM_AUTO) return PLUQ_MM_TENSOR;
+    return kind;
+}
+
+}  // namespace
+}  // namespace pluq
+
+using namespace pluq;
+
+extern "C" {
+
+const char *pluq_status_string(int s)
+{
+    switch (s) {
+        case PLUQ_OK: return "ok";
+        case PLUQ_EINVAL: return "invalid argument";
+        case PLUQ_ENOTPRIME: return "modulus is not a prime in [2, 2^31)";
+        case PLUQ_ERANGE: return "matrix entry not reduced modulo p";
+        case PLUQ_ENOMEM: return "workspace too small";
+        case PLUQ_ECUDA: return "CUDA runtime error";
+        case PLUQ_ETIMEOUT: return "bounded device wait gave up";
+        case PLUQ_EINTERNAL: return "internal consistency check failed";
+        case PLUQ_EUNSUPPORTED: return "kernel form not available";
+        default: return "unknown status";
+    }
+}
+
+int pluq_tensor_limbs(uint32_t p) { return limbs_for_prime(p); }
+int64_t pluq_leaf_max_rows(void) { return LEAF_MAX; }
+int64_t pluq_leaf_max_cols(void) { return LEAF_MAX; }
+
+pluq_status pluq_workspace_size(int64_t m, int64_t n, uint32_t p, size_t *h_bytes)
+{
+    if (m < 0 || n < 0 || !h_bytes) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    // the tensor form's scratch bounds the SIMT form's too
+    *h_bytes = layout(m, n, p, PLUQ_MM_TENSOR).total;
+    return PLUQ_OK;
+}
+
+pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                       int32_t *d_perm_p, int32_t *d_perm_q, int64_t *h_rank, void *d_work,
+                       size_t ws_bytes, int mm_kind, void *stream)
+{
+    if (m < 0 || n < 0 || !h_rank) return PLUQ_EINVAL;
+    if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return PLUQ_EINVAL;
+    if (mm_kind < PLUQ_MM_AUTO || mm_kind > PLUQ_MM_TENSOR) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    if ((m > 0 && !d_perm_p) || (n > 0 && !d_perm_q)) return PLUQ_EINVAL;
+    if (m > 0 && n > 0 && (!d_A || lda < n)) return PLUQ_EINVAL;
+    const int kind = resolve_kind(mm_kind);
+    Layout L = layout(m, n, p, kind);
+    if (!d_work || ws_bytes < L.total) return PLUQ_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    *h_rank = 0;
+    if (m == 0 || n == 0) {
+        PLUQ_TRY(launch_iota(d_perm_p, m, st));
+        PLUQ_TRY(launch_iota(d_perm_q, n, st));
+        return PLUQ_OK;
+    }
+    char *w = (char *)d_work;
+    Ctx c;
+    c.F = make_field(p);
+    c.kind = kind;
+    c.st = st;
+    c.gather = (uint32_t *)w; w += L.gather;
+    c.icopy = (uint32_t *)w; w += L.icopy;
+    c.smap = (int32_t *)w;
+    c.tmap = c.smap + m;
+    w += L.maps;
+    c.vstack = (int32_t *)w;
+    c.vcap = L.vstack / 4;
+    c.vtop = 0;
+    w += L.vstack;
+    c.d_rank = (int32_t *)w; w += L.small;
+    c.ar.base = w;
+    c.ar.size = L.arena;
+    c.ar.off = 0;
+    c.h_rank = pinned_word();
+    if (!c.h_rank) return PLUQ_ECUDA;
+
+    // every entry must already be reduced: checked before anything is written
+    PLUQ_CUDA_TRY(cudaMemsetAsync(c.d_rank, 0, sizeof(int32_t), st));
+    PLUQ_TRY(launch_check_range(d_A, lda, m, n, p, c.d_rank, st));
+    PLUQ_CUDA_TRY(cudaMemcpyAsync(c.h_rank, c.d_rank, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PLUQ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (*c.h_rank != 0) return PLUQ_ERANGE;
+
+    int64_t r = 0;
+    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, r));
+    PLUQ_CUDA_TRY(cudaStreamSynchronize(st));
+    *h_rank = r;
+    return PLUQ_OK;
+}
+
+pluq_status row_rank_profile(const int32_t *d_perm_p, int64_t m, int64_t r, int32_t *d_out,
+                             void *stream)
+{
+    if (r < 0 || r > m || (r > 0 && (!d_perm_p || !d_out))) return PLUQ_EINVAL;
+    return launch_rank_sort(d_perm_p, nullptr, r, d_out, nullptr, (cudaStream_t)stream);
+}
+
+pluq_status col_rank_profile(const int32_t *d_perm_q, int64_t n, int64_t r, int32_t *d_out,
+                             void *stream)
+{
+    if (r < 0 || r > n || (r > 0 && (!d_perm_q || !d_out))) return PLUQ_EINVAL;
+    return launch_rank_sort(d_perm_q, nullptr, r, d_out, nullptr, (cudaStream_t)stream);
+}
+
+pluq_status rank_profile_matrix(const int32_t *d_perm_p, const int32_t *d_perm_q, int64_t m,
+                                int64_t n, int64_t r, int32_t *d_rows, int32_t *d_cols,
+                                void *stream)
+{
+    if (r < 0 || r > m || r > n) return PLUQ_EINVAL;
+    if (r > 0 && (!d_perm_p || !d_perm_q || !d_rows || !d_cols)) return PLUQ_EINVAL;
+    return launch_rank_sort(d_perm_p, d_perm_q, r, d_rows, d_cols, (cudaStream_t)stream);
+}
+
+pluq_status pluq_modmm_workspace_size(int64_t M, int64_t N, int64_t K, uint32_t p, int mm_kind,
+                                      size_t *h_bytes)
+{
+    if (M < 0 || N < 0 || K < 0 || !h_bytes) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    *h_bytes = resolve_kind(mm_kind) == PLUQ_MM_SIMT ? 0 : mm_tc_workspace(M, N, K, p, 1);
+    return PLUQ_OK;
+}
+
+pluq_status pluq_modmm(uint32_t *d_C, int64_t ldc, const uint32_t *d_A, int64_t lda,
+                       const uint32_t *d_B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                       uint32_t p, int assign, int mm_kind, void *d_work, size_t ws_bytes,
+                       void *stream)
+{
+    if (M < 0 || N < 0 || K < 0) return PLUQ_EINVAL;
+    if (mm_kind < PLUQ_MM_AUTO || mm_kind > PLUQ_MM_TENSOR) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    if (M > 0 && N > 0 && (!d_C || ldc < N)) return PLUQ_EINVAL;
+    if (M > 0 && K > 0 && (!d_A || lda < K)) return PLUQ_EINVAL;
+    if (K > 0 && N > 0 && (!d_B || ldb < N)) return PLUQ_EINVAL;
+    const int kind = resolve_kind(mm_kind);
+    Arena ar;
+    ar.base = (char *)d_work;
+    ar.size = d_work ? ws_bytes : 0;
+    ar.off = 0;
+    if (kind != PLUQ_MM_SIMT && ar.size < mm_tc_workspace(M, N, K, p, 1)) return PLUQ_ENOMEM;
+    return launch_mm(kind, Blk{d_C, ldc}, d_A, lda, d_B, ldb, M, N, K, make_field(p),
+                     assign ? MM_ASSIGN : MM_SUB, 1, 0, 0, 0, ar, (cudaStream_t)stream);
+}
+
+pluq_status pluq_trsm_workspace_size(int64_t r, int64_t other, uint32_t p, int mm_kind,
+                                     size_t *h_bytes)
+{
+    if (r < 0 || other < 0 || !h_bytes) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    *h_bytes = trsm_workspace(r, other, p, resolve_kind(mm_kind));
+    return PLUQ_OK;
+}
+
+pluq_status pluq_trsm_left_lower_unit(const uint32_t *d_L, int64_t ldl, uint32_t *d_B,
+                                      int64_t ldb, int64_t r, int64_t N, uint32_t p, int mm_kind,
+                                      void *d_work, size_t ws_bytes, void *stream)
+{
+    if (r < 0 || N < 0) return PLUQ_EINVAL;
+    if (mm_kind < PLUQ_MM_AUTO || mm_kind > PLUQ_MM_TENSOR) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    if (r > 0 && N > 0 && (!d_L || !d_B || ldl < r || ldb < N)) return PLUQ_EINVAL;
+    const int kind = resolve_kind(mm_kind);
+    if (!d_work || ws_bytes < trsm_workspace(r, N, p, kind)) return PLUQ_ENOMEM;
+    Arena ar;
+    ar.base = (char *)d_work;
+    ar.size = ws_bytes;
+    return trsm_left_lower_unit(d_L, ldl, Blk{d_B, ldb}, r, N, make_field(p), kind, ar,
+                                (cudaStream_t)stream);
+}
+
+pluq_status pluq_trsm_right_upper(const uint32_t *d_U, int64_t ldu, uint32_t *d_B, int64_t ldb,
+                                  int64_t M, int64_t r, uint32_t p, int mm_kind, void *d_work,
+                                  size_t ws_bytes, void *stream)
+{
+    if (r < 0 || M < 0) return PLUQ_EINVAL;
+    if (mm_kind < PLUQ_MM_AUTO || mm_kind > PLUQ_MM_TENSOR) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    if (r > 0 && M > 0 && (!d_U || !d_B || ldu < r || ldb < r)) return PLUQ_EINVAL;
+    const int kind = resolve_kind(mm_kind);
+    if (!d_work || ws_bytes < trsm_workspace(r, M, p, kind)) return PLUQ_ENOMEM;
+    Arena ar;
+    ar.base = (char *)d_work;
+    ar.size = ws_bytes;
+    return trsm_right_upper(d_U, ldu, Blk{d_B, ldb}, M, r, make_field(p), kind, ar,
+                            (cudaStream_t)stream);
+}
+
+pluq_status pluq_perm_rows(uint32_t *d_X, int64_t ldx, int64_t count, int64_t width,
+                           const int32_t *d_perm, void *d_work, size_t ws_bytes, void *stream)
+{
+    if (count < 0 || width < 0) return PLUQ_EINVAL;
+    if (count == 0 || width == 0) return PLUQ_OK;
+    if (!d_X || !d_perm || ldx < width) return PLUQ_EINVAL;
+    if (!d_work || ws_bytes < (size_t)count * width * 4) return PLUQ_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    PLUQ_TRY(launch_gather(Blk{(uint32_t *)d_work, width}, d_X, ldx, count, width, d_perm, nullptr,
+                           st));
+    return launch_copy(Blk{d_X, ldx}, (uint32_t *)d_work, width, count, width, st);
+}
+
+pluq_status pluq_perm_cols(uint32_t *d_X, int64_t ldx, int64_t height, int64_t count,
+                           const int32_t *d_perm, void *d_work, size_t ws_bytes, void *stream)
+{
+    if (count < 0 || height < 0) return PLUQ_EINVAL;
+    if (count == 0 || height == 0) return PLUQ_OK;
+    if (!d_X || !d_perm || ldx < count) return PLUQ_EINVAL;
+    if (!d_work || ws_bytes < (size_t)count * height * 4) return PLUQ_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    PLUQ_TRY(launch_gather(Blk{(uint32_t *)d_work, count}, d_X, ldx, height, count, nullptr,
+                           d_perm, st));
+    return launch_copy(Blk{d_X, ldx}, (uint32_t *)d_work, count, height, count, st);
+}
+
+pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                      int32_t *d_perm_p, int32_t *d_perm_q, int32_t *d_rank, void *stream)
+{
+    if (m < 0 || n < 0 || m > LEAF_MAX || n > LEAF_MAX || !d_rank) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    if ((m > 0 && !d_perm_p) || (n > 0 && !d_perm_q)) return PLUQ_EINVAL;
+    if (m > 0 && n > 0 && (!d_A || lda < n)) return PLUQ_EINVAL;
+    return launch_leaf(d_A, m, n, lda, make_field(p), d_perm_p, d_perm_q, d_rank,
+                       (cudaStream_t)stream);
+}
+
+}  // extern "C"

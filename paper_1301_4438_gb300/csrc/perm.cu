@@ -1,0 +1,205 @@
+// Data movement of Algorithm 1 (Sec. 2): PermR / PermC on blocks, the final
+// block permutations S and T, composition of P and Q from the four recursive
+// calls, and the rank-profile read-outs of Sec. 4.  All HBM-bound: each
+// element is read once and written once per pass, rows are walked with
+// consecutive threads on consecutive columns (coalesced), 4 columns per thread.
+#include "common.cuh"
+
+namespace pluq {
+namespace {
+
+constexpr int GT = 256;      // threads per block
+constexpr int GC = 4 * GT;   // columns per block
+
+__global__ void gather_kernel(uint32_t *__restrict__ dst, int64_t ldd,
+                              const uint32_t *__restrict__ src, int64_t lds, int64_t rows,
+                              int64_t cols, const int32_t *__restrict__ rmap,
+                              const int32_t *__restrict__ cmap)
+{
+    const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+        const int64_t si = rmap ? rmap[i] : i;
+        const uint32_t *srow = src + si * lds;
+        uint32_t *drow = dst + i * ldd;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int64_t j = c0 + (int64_t)s * GT;
+            if (j < cols) drow[j] = srow[cmap ? cmap[j] : j];
+        }
+    }
+}
+
+__global__ void fill_kernel(uint32_t *__restrict__ dst, int64_t ldd, int64_t rows, int64_t cols,
+                            uint32_t v)
+{
+    const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int64_t j = c0 + (int64_t)s * GT;
+            if (j < cols) dst[i * ldd + j] = v;
+        }
+    }
+}
+
+// Algorithm 1, final step: P = Diag(P1 diag(I,P2), P3 diag(I,P4)) S and
+// Q = T Diag(diag(I,Q3) Q1, diag(I,Q4) Q2), with the row map of S and column
+// map of T written out for the S^T A T^T pass.  A null sub-permutation is the
+// identity (its recursive call had an empty block).
+struct ComposeArgs {
+    const int32_t *p1, *p2, *p3, *p4, *q1, *q2, *q3, *q4;
+    int32_t *p, *q, *smap, *tmap;
+    int64_t m, n, k, h, r1, r2, r3, r4;
+};
+
+__device__ __forceinline__ int32_t idx_or(const int32_t *v, int64_t i)
+{
+    return v ? v[i] : (int32_t)i;
+}
+
+__global__ void compose_kernel(ComposeArgs a)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.m) {
+        const int64_t i = t;
+        // S: [0, r1+r2) | [k, k+r3+r4) | [r1+r2, k) | [k+r3+r4, m)
+        int64_t s;
+        const int64_t top = a.r1 + a.r2, bot = a.r3 + a.r4;
+        if (i < top) s = i;
+        else if (i < top + bot) s = a.k + (i - top);
+        else if (i < a.k + bot) s = i - bot;
+        else s = i;
+        a.smap[i] = (int32_t)s;
+        int32_t d;
+        if (s < a.k) {
+            d = s < a.r1 ? idx_or(a.p1, s) : idx_or(a.p1, a.r1 + idx_or(a.p2, s - a.r1));
+        } else {
+            int64_t u = s - a.k;
+            d = (int32_t)a.k + (u < a.r3 ? idx_or(a.p3, u) : idx_or(a.p3, a.r3 + idx_or(a.p4, u - a.r3)));
+        }
+        a.p[i] = d;
+    }
+    if (t < a.n) {
+        const int64_t j = t;
+        // T: [0,r1) | [h,h+r2) | [r1,r1+r3) | [h+r2,h+r2+r4) | [r1+r3,h) | [h+r2+r4,n)
+        int64_t c;
+        const int64_t r1 = a.r1, r2 = a.r2, r3 = a.r3, r4 = a.r4, h = a.h;
+        if (j < r1) c = j;
+        else if (j < r1 + r2) c = h + (j - r1);
+        else if (j < r1 + r2 + r3) c = r1 + (j - r1 - r2);
+        else if (j < r1 + r2 + r3 + r4) c = h + r2 + (j - r1 - r2 - r3);
+        else if (j < h + r2 + r4) c = r1 + r3 + (j - r1 - r2 - r3 - r4);
+        else c = j;
+        a.tmap[j] = (int32_t)c;
+        int32_t d;
+        if (c < h) {
+            d = c < r1 ? idx_or(a.q1, c) : idx_or(a.q1, r1 + idx_or(a.q3, c - r1));
+        } else {
+            int64_t u = c - h;
+            d = (int32_t)h + (u < r2 ? idx_or(a.q2, u) : idx_or(a.q2, r2 + idx_or(a.q4, u - r2)));
+        }
+        a.q[j] = d;
+    }
+}
+
+__global__ void iota_kernel(int32_t *v, int64_t n)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) v[t] = (int32_t)t;
+}
+
+// Sorted read-out without scratch: the position of pivot t is the number of
+// pivots with a smaller key (keys are distinct row / column indices).
+__global__ void rank_sort_kernel(const int32_t *__restrict__ key, const int32_t *__restrict__ val,
+                                 int64_t r, int32_t *__restrict__ out_key,
+                                 int32_t *__restrict__ out_val)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= r) return;
+    const int32_t kt = key[t];
+    int64_t pos = 0;
+    for (int64_t u = 0; u < r; ++u) pos += key[u] < kt;
+    out_key[pos] = kt;
+    if (out_val) out_val[pos] = val[t];
+}
+
+__global__ void check_range_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t m,
+                                   int64_t n, uint32_t p, int32_t *flag)
+{
+    const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
+    for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int64_t j = c0 + (int64_t)s * GT;
+            if (j < n && A[i * lda + j] >= p) atomicExch(flag, 1);
+        }
+}
+
+dim3 grid2d(int64_t rows, int64_t cols)
+{
+    int64_t gy = rows < 65535 ? rows : 65535;
+    return dim3((unsigned)ceil_div(cols, GC), (unsigned)(gy > 0 ? gy : 1));
+}
+
+}  // namespace
+
+pluq_status launch_gather(Blk dst, const uint32_t *src, int64_t lds, int64_t rows, int64_t cols,
+                          const int32_t *rmap, const int32_t *cmap, cudaStream_t st)
+{
+    if (rows <= 0 || cols <= 0) return PLUQ_OK;
+    gather_kernel<<<grid2d(rows, cols), GT, 0, st>>>(dst.ptr, dst.ld, src, lds, rows, cols, rmap,
+                                                     cmap);
+    return last_launch();
+}
+
+pluq_status launch_copy(Blk dst, const uint32_t *src, int64_t lds, int64_t rows, int64_t cols,
+                        cudaStream_t st)
+{
+    return launch_gather(dst, src, lds, rows, cols, nullptr, nullptr, st);
+}
+
+pluq_status launch_zero(Blk dst, int64_t rows, int64_t cols, cudaStream_t st)
+{
+    if (rows <= 0 || cols <= 0) return PLUQ_OK;
+    fill_kernel<<<grid2d(rows, cols), GT, 0, st>>>(dst.ptr, dst.ld, rows, cols, 0u);
+    return last_launch();
+}
+
+pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return PLUQ_OK;
+    iota_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(v, n);
+    return last_launch();
+}
+
+pluq_status launch_compose(const int32_t *p1, const int32_t *p2, const int32_t *p3,
+                           const int32_t *p4, const int32_t *q1, const int32_t *q2,
+                           const int32_t *q3, const int32_t *q4, int32_t *p, int32_t *q,
+                           int32_t *smap, int32_t *tmap, int64_t m, int64_t n, int64_t k,
+                           int64_t h, int64_t r1, int64_t r2, int64_t r3, int64_t r4,
+                           cudaStream_t st)
+{
+    ComposeArgs a{p1, p2, p3, p4, q1, q2, q3, q4, p, q, smap, tmap, m, n, k, h, r1, r2, r3, r4};
+    int64_t len = m > n ? m : n;
+    if (len <= 0) return PLUQ_OK;
+    compose_kernel<<<(unsigned)ceil_div(len, 256), 256, 0, st>>>(a);
+    return last_launch();
+}
+
+pluq_status launch_rank_sort(const int32_t *key, const int32_t *val, int64_t r, int32_t *out_key,
+                             int32_t *out_val, cudaStream_t st)
+{
+    if (r <= 0) return PLUQ_OK;
+    rank_sort_kernel<<<(unsigned)ceil_div(r, 256), 256, 0, st>>>(key, val, r, out_key, out_val);
+    return last_launch();
+}
+
+pluq_status launch_check_range(const uint32_t *A, int64_t lda, int64_t m, int64_t n, uint32_t p,
+                               int32_t *flag, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return PLUQ_OK;
+    check_range_kernel<<<grid2d(m, n), GT, 0, st>>>(A, lda, m, n, p, flag);
+    return last_launch();
+}
+
+}  // namespace pluq

@@ -1,0 +1,275 @@
+"""Thin Python binding of libpluq (include/pluq.h).
+
+Argument marshalling only: torch tensors are passed as raw device pointers and
+the current CUDA stream; every step of the computation runs in the library's
+CUDA kernels.  The library is loaded from this package directory on first use;
+if it is missing or no CUDA device is present the calls raise.  There is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpluq.so")
+_lock = threading.Lock()
+_lib = None
+
+MM_AUTO, MM_SIMT, MM_TENSOR = 0, 1, 2
+_KIND = {"auto": MM_AUTO, "simt": MM_SIMT, "tensor": MM_TENSOR}
+
+_c_i64 = ctypes.c_int64
+_c_u32 = ctypes.c_uint32
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+
+_SIGS = {
+    "pluq_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pluq_tensor_limbs": (ctypes.c_int, [_c_u32]),
+    "pluq_leaf_max_rows": (_c_i64, []),
+    "pluq_leaf_max_cols": (_c_i64, []),
+    "pluq_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_u32, _szp]),
+    "pluq_mod_p": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_u32, _vp, _vp, _i64p, _vp,
+                                  ctypes.c_size_t, ctypes.c_int, _vp]),
+    "row_rank_profile": (ctypes.c_int, [_vp, _c_i64, _c_i64, _vp, _vp]),
+    "col_rank_profile": (ctypes.c_int, [_vp, _c_i64, _c_i64, _vp, _vp]),
+    "rank_profile_matrix": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp]),
+    "pluq_modmm_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _c_u32, ctypes.c_int,
+                                                 _szp]),
+    "pluq_modmm": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _c_i64, _c_i64, _c_i64,
+                                  _c_u32, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "pluq_trsm_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_u32, ctypes.c_int, _szp]),
+    "pluq_trsm_left_lower_unit": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _c_i64, _c_i64, _c_u32,
+                                                 ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "pluq_trsm_right_upper": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _c_i64, _c_i64, _c_u32,
+                                             ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "pluq_perm_rows": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, ctypes.c_size_t,
+                                      _vp]),
+    "pluq_perm_cols": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, ctypes.c_size_t,
+                                      _vp]),
+    "pluq_leaf": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_u32, _vp, _vp, _vp, _vp]),
+}
+
+
+class PluqError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+def load():
+    """Load libpluq.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libpluq.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def status_string(status: int) -> str:
+    return load().pluq_status_string(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise PluqError(status, what)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else ctypes.c_void_p(0)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libpluq works on CUDA tensors only")
+
+
+def _u32_view(A: torch.Tensor) -> torch.Tensor:
+    """uint32 data are carried in int32 tensors (same bits)."""
+    if A.dtype not in (torch.int32,) and getattr(torch, "uint32", None) is not A.dtype:
+        raise TypeError("matrix must be int32/uint32 holding residues in [0, p)")
+    return A
+
+
+def tensor_limbs(p: int) -> int:
+    return int(load().pluq_tensor_limbs(p))
+
+
+def leaf_max() -> tuple:
+    lib = load()
+    return int(lib.pluq_leaf_max_rows()), int(lib.pluq_leaf_max_cols())
+
+
+def pluq_workspace_size(m: int, n: int, p: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().pluq_workspace_size(m, n, p, ctypes.byref(out)), "pluq_workspace_size")
+    return int(out.value)
+
+
+def pluq_mod_p(A: torch.Tensor, p: int, mm: str = "auto", workspace: torch.Tensor = None,
+               stream=None):
+    """In-place PLUQ of A (m x n int32 on the GPU, residues in [0, p)).
+    Returns (perm_p, perm_q, r); A holds the packed [L\\U V; M 0]."""
+    _need_cuda(A)
+    _u32_view(A)
+    m, n = A.shape
+    lda = A.stride(0) if m > 0 else max(n, 1)
+    if A.numel() and A.stride(1) != 1:
+        raise ValueError("rows of A must be contiguous")
+    dev = A.device
+    pp = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    pq = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ws = pluq_workspace_size(m, n, p)
+    if workspace is None or workspace.numel() < ws:
+        workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+    r = ctypes.c_int64(0)
+    st = load().pluq_mod_p(_ptr(A), m, n, lda, p, _ptr(pp), _ptr(pq), ctypes.byref(r),
+                           _ptr(workspace), workspace.numel(), _KIND[mm], _stream(stream))
+    _check(st, "pluq_mod_p")
+    return pp[:m], pq[:n], int(r.value)
+
+
+def row_rank_profile(perm_p: torch.Tensor, r: int, stream=None) -> torch.Tensor:
+    _need_cuda(perm_p)
+    out = torch.empty(max(r, 1), dtype=torch.int32, device=perm_p.device)
+    _check(load().row_rank_profile(_ptr(perm_p), perm_p.numel(), r, _ptr(out), _stream(stream)),
+           "row_rank_profile")
+    return out[:r]
+
+
+def col_rank_profile(perm_q: torch.Tensor, r: int, stream=None) -> torch.Tensor:
+    _need_cuda(perm_q)
+    out = torch.empty(max(r, 1), dtype=torch.int32, device=perm_q.device)
+    _check(load().col_rank_profile(_ptr(perm_q), perm_q.numel(), r, _ptr(out), _stream(stream)),
+           "col_rank_profile")
+    return out[:r]
+
+
+def rank_profile_matrix(perm_p: torch.Tensor, perm_q: torch.Tensor, r: int, stream=None):
+    _need_cuda(perm_p, perm_q)
+    rows = torch.empty(max(r, 1), dtype=torch.int32, device=perm_p.device)
+    cols = torch.empty(max(r, 1), dtype=torch.int32, device=perm_p.device)
+    _check(load().rank_profile_matrix(_ptr(perm_p), _ptr(perm_q), perm_p.numel(), perm_q.numel(),
+                                      r, _ptr(rows), _ptr(cols), _stream(stream)),
+           "rank_profile_matrix")
+    return rows[:r], cols[:r]
+
+
+def modmm_workspace_size(M: int, N: int, K: int, p: int, mm: str = "auto") -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().pluq_modmm_workspace_size(M, N, K, p, _KIND[mm], ctypes.byref(out)),
+           "pluq_modmm_workspace_size")
+    return int(out.value)
+
+
+def pluq_modmm(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, p: int, assign: bool = False,
+               mm: str = "auto", workspace: torch.Tensor = None, stream=None):
+    """C <- C - A B (or A B) mod p, in place on C."""
+    _need_cuda(C, A, B)
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K or tuple(C.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    ws = modmm_workspace_size(M, N, K, p, mm)
+    if ws and (workspace is None or workspace.numel() < ws):
+        workspace = torch.empty(ws, dtype=torch.uint8, device=C.device)
+    wsn = workspace.numel() if workspace is not None else 0
+    _check(load().pluq_modmm(_ptr(C), C.stride(0) if M else max(N, 1), _ptr(A),
+                             A.stride(0) if M else max(K, 1), _ptr(B),
+                             B.stride(0) if K else max(N, 1), M, N, K, p, int(assign), _KIND[mm],
+                             _ptr(workspace), wsn, _stream(stream)), "pluq_modmm")
+    return C
+
+
+def _trsm_ws(r, other, p, mm, workspace, dev):
+    out = ctypes.c_size_t(0)
+    _check(load().pluq_trsm_workspace_size(r, other, p, _KIND[mm], ctypes.byref(out)),
+           "pluq_trsm_workspace_size")
+    if workspace is None or workspace.numel() < out.value:
+        workspace = torch.empty(max(out.value, 1), dtype=torch.uint8, device=dev)
+    return workspace
+
+
+def pluq_trsm_left_lower_unit(L: torch.Tensor, B: torch.Tensor, p: int, mm: str = "auto",
+                              workspace=None, stream=None):
+    """B <- L^{-1} B in place (L unit lower, diagonal not read)."""
+    _need_cuda(L, B)
+    r, N = B.shape
+    ws = _trsm_ws(r, N, p, mm, workspace, B.device)
+    _check(load().pluq_trsm_left_lower_unit(_ptr(L), L.stride(0) if r else 1, _ptr(B),
+                                            B.stride(0) if r else max(N, 1), r, N, p, _KIND[mm],
+                                            _ptr(ws), ws.numel(), _stream(stream)),
+           "pluq_trsm_left_lower_unit")
+    return B
+
+
+def pluq_trsm_right_upper(U: torch.Tensor, B: torch.Tensor, p: int, mm: str = "auto",
+                          workspace=None, stream=None):
+    """B <- B U^{-1} in place (U upper, nonzero diagonal)."""
+    _need_cuda(U, B)
+    M, r = B.shape
+    ws = _trsm_ws(r, M, p, mm, workspace, B.device)
+    _check(load().pluq_trsm_right_upper(_ptr(U), U.stride(0) if r else 1, _ptr(B),
+                                        B.stride(0) if M else max(r, 1), M, r, p, _KIND[mm],
+                                        _ptr(ws), ws.numel(), _stream(stream)),
+           "pluq_trsm_right_upper")
+    return B
+
+
+def pluq_perm_rows(X: torch.Tensor, perm: torch.Tensor, workspace=None, stream=None):
+    _need_cuda(X, perm)
+    count, width = X.shape
+    if workspace is None:
+        workspace = torch.empty(max(count * width * 4, 1), dtype=torch.uint8, device=X.device)
+    _check(load().pluq_perm_rows(_ptr(X), X.stride(0) if count else max(width, 1), count, width,
+                                 _ptr(perm), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "pluq_perm_rows")
+    return X
+
+
+def pluq_perm_cols(X: torch.Tensor, perm: torch.Tensor, workspace=None, stream=None):
+    _need_cuda(X, perm)
+    height, count = X.shape
+    if workspace is None:
+        workspace = torch.empty(max(count * height * 4, 1), dtype=torch.uint8, device=X.device)
+    _check(load().pluq_perm_cols(_ptr(X), X.stride(0) if height else max(count, 1), height, count,
+                                 _ptr(perm), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "pluq_perm_cols")
+    return X
+
+
+def pluq_leaf(A: torch.Tensor, p: int, stream=None):
+    """Base case on a block of at most pluq_leaf_max_rows() x pluq_leaf_max_cols(), in place.
+    Returns (perm_p, perm_q, r) with r read back after the stream synchronises."""
+    _need_cuda(A)
+    m, n = A.shape
+    dev = A.device
+    pp = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    pq = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    rk = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(load().pluq_leaf(_ptr(A), m, n, A.stride(0) if m else max(n, 1), p, _ptr(pp), _ptr(pq),
+                            _ptr(rk), _stream(stream)), "pluq_leaf")
+    return pp[:m], pq[:n], int(rk.item())

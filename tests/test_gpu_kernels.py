@@ -1,0 +1,208 @@
+"""Per-kernel parity of the CUDA path against the CPU oracle (bit-exact).
+
+Every case calls the C-ABI library through its binding and compares element
+by element with the oracle on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1301_4438_gb300 import pluq, workloads as W
+from tests import brute
+
+pytestmark = pytest.mark.gpu
+PRIMES = [2, 3, 251, 65521, 8388593, 2147483647]
+KINDS = ["simt", "tensor"]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.int32)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.uint32)
+
+
+def _structured(g, m, n, p):
+    kind = int(g.integers(0, 4))
+    if kind == 0:
+        return g.integers(0, p, (m, n)).astype(np.uint32)
+    if kind == 1:
+        return (g.integers(0, p, (m, n)) * (g.random((m, n)) < 0.1)).astype(np.uint32)
+    if kind == 2:
+        r = int(g.integers(0, min(m, n) + 1))
+        return W.planted(m, n, r, p, int(g.integers(1 << 30)))[0]
+    A = g.integers(0, p, (m, n))
+    A[g.random(m) < 0.3] = 0
+    A[:, g.random(n) < 0.3] = 0
+    return A.astype(np.uint32)
+
+
+# ------------------------------------------------------------------ leaf --
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_leaf_matches_oracle(p):
+    g = np.random.Generator(np.random.PCG64(p + 1))
+    lm, ln = pluq.leaf_max()
+    shapes = [(1, 1), (1, 128), (128, 1), (128, 128), (127, 65), (3, 100), (64, 64), (2, 2)]
+    shapes += [(int(g.integers(1, lm + 1)), int(g.integers(1, ln + 1))) for _ in range(12)]
+    for (m, n) in shapes:
+        A = _structured(g, m, n, p)
+        LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+        d = dev(A)
+        pp, pq, r = pluq.pluq_leaf(d, p)
+        assert r == r0, (m, n)
+        assert np.array_equal(pp.cpu().numpy(), pp0), (m, n)
+        assert np.array_equal(pq.cpu().numpy(), pq0), (m, n)
+        assert np.array_equal(host(d), LU0), (m, n)
+
+
+def test_leaf_exhaustive_gf2_4x4():
+    As = brute.all_matrices(4, 4, 2)[::5]
+    for A in As:
+        A = A.astype(np.uint32)
+        LU0, pp0, pq0, r0 = oracle.pluq(A, 2)
+        d = dev(A)
+        pp, pq, r = pluq.pluq_leaf(d, 2)
+        assert r == r0 and np.array_equal(pp.cpu().numpy(), pp0)
+        assert np.array_equal(pq.cpu().numpy(), pq0) and np.array_equal(host(d), LU0)
+
+
+def test_leaf_in_place_inside_larger_matrix():
+    p = 65521
+    g = np.random.Generator(np.random.PCG64(5))
+    big = g.integers(0, p, (200, 300)).astype(np.uint32)
+    sub = W.planted(100, 90, 40, p, 3)[0]
+    big[50:150, 70:160] = sub
+    d = dev(big)
+    pp, pq, r = pluq.pluq_leaf(d[50:150, 70:160], p)
+    LU0, pp0, pq0, r0 = oracle.pluq(sub, p)
+    out = host(d)
+    assert r == r0 and np.array_equal(out[50:150, 70:160], LU0)
+    mask = np.ones_like(big, dtype=bool)
+    mask[50:150, 70:160] = False
+    assert np.array_equal(out[mask], big[mask])      # nothing outside the block touched
+
+
+# ---------------------------------------------------------------- modmm --
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("p", PRIMES)
+def test_modmm_matches_oracle(kind, p):
+    g = np.random.Generator(np.random.PCG64(1000 + p))
+    shapes = [(1, 1, 1), (64, 64, 64), (130, 257, 129), (7, 300, 1000), (300, 5, 77),
+              (256, 256, 1500), (1, 513, 64), (200, 200, 0)]
+    for (M, N, K) in shapes:
+        A = g.integers(0, p, (M, K)).astype(np.uint32)
+        B = g.integers(0, p, (K, N)).astype(np.uint32)
+        C = g.integers(0, p, (M, N)).astype(np.uint32)
+        want = oracle.matmul_sub(C, A, B, p)
+        dC = dev(C)
+        pluq.pluq_modmm(dC, dev(A), dev(B), p, mm=kind)
+        assert np.array_equal(host(dC), want), (M, N, K)
+        # assign form: C <- A B
+        want2 = oracle.matmul_sub(np.zeros((M, N), np.uint32), A, B, p)
+        want2 = ((p - want2.astype(np.int64)) % p).astype(np.uint32)
+        dC2 = dev(C)
+        pluq.pluq_modmm(dC2, dev(A), dev(B), p, assign=True, mm=kind)
+        assert np.array_equal(host(dC2), want2), (M, N, K)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_modmm_strided_blocks(kind):
+    p = 8388593
+    g = np.random.Generator(np.random.PCG64(8))
+    big = g.integers(0, p, (700, 900)).astype(np.uint32)
+    d = dev(big)
+    # C = rows 400..650 x cols 500..880, A = rows 400..650 x cols 0..300, B = rows 0..300 x 500..880
+    C, A, B = big[400:650, 500:880], big[400:650, 0:300], big[0:300, 500:880]
+    want = oracle.matmul_sub(C, A, B, p)
+    pluq.pluq_modmm(d[400:650, 500:880], d[400:650, 0:300], d[0:300, 500:880], p, mm=kind)
+    out = host(d)
+    assert np.array_equal(out[400:650, 500:880], want)
+    mask = np.ones_like(big, dtype=bool)
+    mask[400:650, 500:880] = False
+    assert np.array_equal(out[mask], big[mask])
+
+
+# ----------------------------------------------------------------- trsm --
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("p", [3, 65521, 2147483647])
+def test_trsm_matches_oracle(kind, p):
+    g = np.random.Generator(np.random.PCG64(2000 + p))
+    for (r, other) in [(1, 5), (63, 10), (64, 64), (65, 200), (200, 130), (517, 300)]:
+        L = g.integers(0, p, (r, r)).astype(np.uint32)
+        B = g.integers(0, p, (r, other)).astype(np.uint32)
+        want = oracle.trsm_left_lower_unit(L, B, p)
+        dB = dev(B)
+        pluq.pluq_trsm_left_lower_unit(dev(L), dB, p, mm=kind)
+        assert np.array_equal(host(dB), want), ("left", r, other)
+        U = np.triu(g.integers(1, p, (r, r))).astype(np.uint32)
+        U = (U + np.tril(g.integers(0, p, (r, r)), -1)).astype(np.uint32)   # lower part ignored
+        B2 = g.integers(0, p, (other, r)).astype(np.uint32)
+        want2 = oracle.trsm_right_upper(np.triu(U), B2, p)
+        dB2 = dev(B2)
+        pluq.pluq_trsm_right_upper(dev(U), dB2, p, mm=kind)
+        assert np.array_equal(host(dB2), want2), ("right", r, other)
+
+
+# ---------------------------------------------------------- permutations --
+
+def test_perm_rows_cols():
+    g = np.random.Generator(np.random.PCG64(9))
+    for (h, w) in [(1, 1), (5, 1000), (1000, 3), (257, 513)]:
+        X = g.integers(0, 1 << 31, (h, w)).astype(np.uint32)
+        pr = g.permutation(h).astype(np.int32)
+        pc = g.permutation(w).astype(np.int32)
+        d = dev(X)
+        pluq.pluq_perm_rows(d, torch.from_numpy(pr).cuda())
+        assert np.array_equal(host(d), X[pr])
+        pluq.pluq_perm_cols(d, torch.from_numpy(pc).cuda())
+        assert np.array_equal(host(d), X[pr][:, pc])
+
+
+# -------------------------------------------------------- rank profiles --
+
+def test_rank_profile_readouts():
+    p = 65521
+    A, pl = W.planted(300, 200, 120, p, 11)
+    d = dev(A)
+    pp, pq, r = pluq.pluq_mod_p(d, p, mm="simt")
+    assert r == 120
+    rows = pluq.row_rank_profile(pp, r).cpu().numpy()
+    cols = pluq.col_rank_profile(pq, r).cpu().numpy()
+    assert np.array_equal(rows, np.sort(pl.rows))
+    assert np.array_equal(cols, np.sort(pl.cols))
+    rr, cc = pluq.rank_profile_matrix(pp, pq, r)
+    order = np.argsort(pl.rows)
+    assert np.array_equal(rr.cpu().numpy(), pl.rows[order])
+    assert np.array_equal(cc.cpu().numpy(), pl.cols[order])
+
+
+# -------------------------------------------------------------- errors --
+
+def test_error_statuses_leave_input_untouched():
+    p = 65521
+    A = np.full((10, 10), 5, dtype=np.uint32)
+    A[3, 4] = p                      # not reduced
+    d = dev(A)
+    with pytest.raises(pluq.PluqError) as e:
+        pluq.pluq_mod_p(d, p)
+    assert e.value.status == -3
+    assert np.array_equal(host(d), A)
+    with pytest.raises(pluq.PluqError) as e:
+        pluq.pluq_mod_p(dev(np.zeros((4, 4), np.uint32)), 65535)
+    assert e.value.status == -2
+    # a too-small workspace (the binding would replace it; call the library directly)
+    lib = pluq.load()
+    import ctypes
+    r = ctypes.c_int64(0)
+    z = dev(np.zeros((64, 64), np.uint32))
+    pp = torch.empty(64, dtype=torch.int32, device="cuda")
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    st = lib.pluq_mod_p(ctypes.c_void_p(z.data_ptr()), 64, 64, 64, p, ctypes.c_void_p(pp.data_ptr()),
+                        ctypes.c_void_p(pp.data_ptr()), ctypes.byref(r), ctypes.c_void_p(ws.data_ptr()),
+                        16, 0, ctypes.c_void_p(0))
+    assert st == -4

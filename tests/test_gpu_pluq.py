@@ -1,0 +1,111 @@
+"""End-to-end parity of pluq_mod_p (CUDA path through the C-ABI) with the oracle.
+
+Small and medium sizes (several leaves and ragged tails) are compared element
+by element with the oracle.  Full-size workloads are checked with the
+size-independent certificate of tests/certify.py (reconstruction, LEU
+triangularity => rank profile matrix, Algorithm 1's pivot order), plus the
+planted rank profile where the input was built with one.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1301_4438_gb300 import pluq, workloads as W
+from tests.certify import certify
+
+pytestmark = pytest.mark.gpu
+KINDS = ["simt", "tensor"]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.int32)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.uint32)
+
+
+def run(A, p, kind):
+    d = dev(A)
+    pp, pq, r = pluq.pluq_mod_p(d, p, mm=kind)
+    torch.cuda.synchronize()
+    return host(d), pp.cpu().numpy(), pq.cpu().numpy(), r
+
+
+def assert_same(A, p, kind):
+    LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+    LU, pp, pq, r = run(A, p, kind)
+    assert r == r0
+    assert np.array_equal(pp, pp0)
+    assert np.array_equal(pq, pq0)
+    assert np.array_equal(LU, LU0)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("m,n,r,p", [
+    (300, 257, 150, 65521), (257, 300, 257, 65521), (129, 1000, 100, 8388593),
+    (1000, 129, 129, 2147483647), (512, 512, 300, 65521), (600, 450, 0, 251),
+    (1, 700, 1, 7), (700, 1, 1, 65521), (2, 900, 2, 3), (384, 384, 384, 2147483647),
+])
+def test_pluq_planted_matches_oracle(kind, m, n, r, p):
+    A, pl = W.planted(m, n, r, p, seed=m * 7 + n * 3 + r)
+    assert_same(A, p, kind)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("m,n,p", [(520, 390, 65521), (260, 260, 2), (333, 777, 2147483647)])
+def test_pluq_dense_and_structured(kind, m, n, p):
+    g = np.random.Generator(np.random.PCG64(m + n + p))
+    A = g.integers(0, p, (m, n)).astype(np.uint32)
+    assert_same(A, p, kind)
+    # zero rows / columns and duplicated rows
+    B = A.copy()
+    B[g.random(m) < 0.25] = 0
+    B[:, g.random(n) < 0.25] = 0
+    B[m // 2] = B[1]
+    assert_same(B, p, kind)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_pluq_empty_and_zero(kind):
+    for (m, n) in [(0, 0), (0, 10), (10, 0)]:
+        d = torch.zeros((m, n), dtype=torch.int32, device="cuda")
+        pp, pq, r = pluq.pluq_mod_p(d, 65521, mm=kind)
+        assert r == 0 and pp.numel() == m and pq.numel() == n
+    LU, pp, pq, r = run(np.zeros((300, 200), np.uint32), 65521, kind)
+    assert r == 0 and not LU.any()
+    assert np.array_equal(pp, np.arange(300)) and np.array_equal(pq, np.arange(200))
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_config_planted_256(kind):
+    cfg = W.CONFIGS["planted_256"]
+    A, pl = W.make(cfg)
+    assert_same(A, cfg.p, kind)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_config_dense_4096(kind):
+    """4096 x 4096 uniform mod 65521 at full size: certificate."""
+    cfg = W.CONFIGS["dense_4096"]
+    A, _ = W.make(cfg)
+    LU, pp, pq, r = run(A, cfg.p, kind)
+    assert certify(A, cfg.p, LU, pp, pq, r, exact=False, trials=2) == ""
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["planted_16384", "rect_8192x32768"])
+def test_config_large_planted(name):
+    """Full-size planted workloads: certificate and the planted rank profile."""
+    cfg = W.CONFIGS[name]
+    At, pl = W.make(cfg, device="cuda")
+    A32 = At.to(torch.int32)
+    del At
+    A = host(A32)
+    pp, pq, r = pluq.pluq_mod_p(A32, cfg.p, mm="tensor")
+    torch.cuda.synchronize()
+    LU = host(A32)
+    assert r == cfg.r
+    assert certify(A, cfg.p, LU, pp.cpu().numpy(), pq.cpu().numpy(), r, exact=False, trials=1,
+                   expected_col_of_row=pl.rank_profile()) == ""
