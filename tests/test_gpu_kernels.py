@@ -206,3 +206,26 @@ def test_error_statuses_leave_input_untouched():
                         ctypes.c_void_p(pp.data_ptr()), ctypes.byref(r), ctypes.c_void_p(ws.data_ptr()),
                         16, 0, ctypes.c_void_p(0))
     assert st == -4
+
+
+# ------------------------------------------- tensor-core exactness bound --
+
+@pytest.mark.parametrize("p,x", [(65521, 32640), (8388593, 4161408), (2147483647, 1065320320),
+                                 (251, 128)])
+def test_tensor_exact_at_accumulation_bound(p, x):
+    """Residues whose balanced digits have the largest magnitudes the split
+    produces, so every partial sum of a K-chunk reaches the 2^24 bound; and the
+    same with alternating signs (cancellation).  Must stay bit-exact."""
+    assert pluq.tensor_limbs(p) in (1, 2, 3, 4)
+    for K in (64, 256, 320, 512, 1024, 1600):
+        for mixed in (False, True):
+            A = np.full((130, K), x, np.uint32)
+            B = np.full((K, 70), x, np.uint32)
+            if mixed:
+                A[:, 1::2] = p - x
+                B[::3, :] = p - x
+            C = np.zeros((130, 70), np.uint32)
+            want = oracle.matmul_sub(C, A, B, p)
+            dC = dev(C)
+            pluq.pluq_modmm(dC, dev(A), dev(B), p, mm="tensor")
+            assert np.array_equal(host(dC), want), (K, mixed)
