@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark: rank-profile-revealing PLUQ mod p on one GB300 (or N replicas).
+
+One step = one PLUQ decomposition (Algorithm 1, every kernel of the hot path)
+of the workload matrix.  Default workload: 4096 x 4096 uniform mod 65521
+(dense_4096).  Metric: Gfops/s normalised by the classical elimination count
+fops(m, n, r) = 2mnr - (m + n) r^2 + (2/3) r^3.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank factors its own copy (replicas: a single matrix has
+no exchange step worth a collective); value = matrices of all ranks / max time.
+`--impl reference` times the CPU oracle (oracle/) on a bounded sample of the
+same workload, on the host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "PLUQ mod p Gfops/s (mnr-normalised); modular-GEMM % of dense INT8 TC peak"
+UNIT = "Gfops/s"
+
+
+def fops(m, n, r):
+    return 2.0 * m * n * r - (m + n) * r * r + (2.0 / 3.0) * r ** 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense_4096")
+    ap.add_argument("--mm", default="tensor", choices=["tensor", "simt"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle --
+def cpu_oracle_rate(target_s: float = 12.0, p: int = 65521):
+    """Time the oracle as it stands on a bounded square sample of the dense
+    workload (uniform mod p); returns (Gfops/s, seconds, n, cores)."""
+    import oracle
+    from paper_1301_4438_gb300 import workloads as W
+    oracle.build()
+
+    def one(n):
+        A = W.uniform(n, n, p, W.BASE_SEED + 1)
+        t0 = time.perf_counter()
+        LU, pp, pq, r = oracle.pluq(A, p)
+        return time.perf_counter() - t0, r
+
+    t, r = one(384)
+    n = int(384 * (target_s / max(t, 1e-3)) ** (1.0 / 3.0)) // 64 * 64
+    n = max(384, min(n, 2048))
+    t, r = one(n)
+    return fops(n, n, r) / t / 1e9, t, n, os.cpu_count() or 1
+
+
+# ---------------------------------------------------------- roofline input --
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("mm_tc.cu", "common.cuh", "leaf.cu", "perm.cu"):
+        with open(os.path.join(ROOT, "paper_1301_4438_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_class: str, workload: str):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = data.get(f"{kernel_class}:{workload}")
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    except (OSError, ValueError):
+        return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------------- ours --
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1301_4438_gb300 import pluq, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cfg = W.CONFIGS[args.workload]
+    if cfg.kind == "uniform":
+        A_host_np, _ = W.make(cfg)
+        A0 = torch.from_numpy(A_host_np.astype(np.int32)).to(dev)
+    else:
+        At, _ = W.make(cfg, device=str(dev))
+        A0 = At.to(torch.int32)
+        del At
+        A_host_np = A0.cpu().numpy()
+    m, n, p = cfg.m, cfg.n, cfg.p
+    A = torch.empty_like(A0)
+    ws = torch.empty(pluq.pluq_workspace_size(m, n, p), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(mm):
+        A.copy_(A0)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp, pq, r = pluq.pluq_mod_p(A, p, mm=mm, workspace=ws)
+        e1.record(stream)
+        return e0, e1, r
+
+    for _ in range(args.warmup):
+        step(args.mm)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (device events around each decomposition)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = pluq.pluq_launch_count()
+    pluq.pluq_profile_enable(True)
+    evs = [step(args.mm) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    pluq.pluq_profile_enable(False)
+    launches = pluq.pluq_launch_count() - launches0
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b, _ in evs]
+    r = evs[-1][2]
+    total_ms = sum(times)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    work = fops(m, n, r)
+    value = world * args.steps * work / (total_ms / 1e3) / 1e9
+
+    # per-class device time inside the timed region
+    classes = {}
+    for name in pluq.PROFILE_CLASSES:
+        nl, ms, w = pluq.pluq_profile_read(name)
+        classes[name] = {"launches": nl, "ms": ms, "work": w}
+    dominant = max(classes, key=lambda k: classes[k]["ms"])
+    hbm_peak, bf16_peak, peak_src = measured_peaks()
+
+    def roofline_for(name):
+        c = classes[name]
+        if c["launches"] == 0 or c["ms"] <= 0:
+            return None
+        per_launch_s = c["ms"] / c["launches"] / 1e3
+        per_launch_work = c["work"] / c["launches"]
+        if name in ("tensor_mm",):
+            bound, unit, peak = "tensor", "TFLOP/s", bf16_peak
+            achieved = per_launch_work / per_launch_s / 1e12
+        elif name in ("move", "split", "leaf"):
+            bound, unit, peak = "hbm", "GB/s", hbm_peak
+            achieved = per_launch_work / per_launch_s / 1e9
+        else:
+            bound, unit, peak = "alu", "Gop/s", None
+            achieved = per_launch_work / per_launch_s / 1e9
+        return {"kernel_class": name, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": (achieved / peak) if peak else None,
+                "traffic": committed_traffic(name, args.workload),
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json burst)" if peak else None,
+                "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6,
+                "share_of_step": c["ms"] / max(sum(times), 1e-9)}
+
+    roof = roofline_for(dominant)
+    roof_mm = roofline_for("tensor_mm") if args.mm == "tensor" else roofline_for("simt_mm")
+
+    # ---------------- plain CUDA-core form on the same workload (context)
+    simt_value = None
+    if args.mm == "tensor" and cfg.kind == "uniform":
+        for _ in range(max(1, args.warmup // 2)):
+            step("simt")
+        torch.cuda.synchronize()
+        sv = [step("simt") for _ in range(max(3, args.steps // 2))]
+        torch.cuda.synchronize()
+        st = [a.elapsed_time(b) for a, b, _ in sv]
+        simt_value = work / (statistics.mean(st) / 1e3) / 1e9
+
+    # ---------------- end to end through the public API with host buffers
+    A_pinned = torch.from_numpy(A_host_np.astype(np.int32)).pin_memory()
+    out_pinned = torch.empty_like(A_pinned).pin_memory()
+    pp_pinned = torch.empty(m, dtype=torch.int32).pin_memory()
+    pq_pinned = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        A.copy_(A_pinned, non_blocking=True)
+        pp, pq, rr = pluq.pluq_mod_p(A, p, mm=args.mm, workspace=ws)
+        out_pinned.copy_(A, non_blocking=True)
+        pp_pinned.copy_(pp, non_blocking=True)
+        pq_pinned.copy_(pq, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e2e_times)
+    e2e = {"value": world * work / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": m * n * 4 + (m + n) * 4,
+           "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, ns, cores = cpu_oracle_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{ns}x{ns} uniform mod {p} (dense recipe at reduced size), one "
+                         f"decomposition, {secs:.1f} s; rank-profile phase single-threaded, "
+                         f"elimination phase OpenMP"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "m": m, "n": n, "p": p, "rank": r,
+                       "recipe": cfg.note, "mm": args.mm,
+                       "limbs": pluq.tensor_limbs(p) if args.mm == "tensor" else None,
+                       "l2": "flushed (256 MiB write) and input restored from a device copy "
+                             "between steps, outside the timed events",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "modular_gemm": roof_mm,
+            "kernel_classes": classes,
+            "plain_cuda_core_value": simt_value,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------------- reference --
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1301_4438_gb300 import workloads as W
+    oracle.build()
+    cfg = W.CONFIGS[args.workload]
+    p = cfg.p
+    # bounded sample: a square uniform matrix sized for ~1/(K+W) of two minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    A = W.uniform(256, 256, p, W.BASE_SEED + 1)
+    t0 = time.perf_counter()
+    oracle.pluq(A, p)
+    t = time.perf_counter() - t0
+    ns = int(256 * (budget / max(t, 1e-3)) ** (1.0 / 3.0)) // 64 * 64
+    ns = max(256, min(ns, 2048))
+    A = W.uniform(ns, ns, p, W.BASE_SEED + 1)
+    times, r = [], 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, _, _, r = oracle.pluq(A, p)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * fops(ns, ns, r) / tot / 1e9
+    cores = os.cpu_count() or 1
+    sample = (f"{ns}x{ns} uniform mod {p} per step (the {cfg.name} recipe at reduced size); "
+              f"rank-profile phase single-threaded, elimination phase OpenMP")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": {"workload": cfg.name, "m": ns, "n": ns, "p": p, "rank": r},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

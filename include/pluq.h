@@ -163,6 +163,22 @@ int64_t pluq_leaf_max_cols(void);
 pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
                       int32_t *d_perm_p, int32_t *d_perm_q, int32_t *d_rank, void *stream);
 
+/*
+ * Instrumentation (no counterpart in the paper).  pluq_launch_count: kernels
+ * launched by this library since the process started.  pluq_profile_enable(1)
+ * starts a session that brackets every launch of the timed kernel classes
+ * with CUDA events on its stream (0 stops recording); pluq_profile_read
+ * synchronises on those events and returns, for one class, the number of
+ * launches, their summed device time in ms and their summed algorithmic work:
+ *   0 tensor-core MM (2 L^2 M N K digit-product flops), 1 SIMT MM (2 M N K),
+ *   2 leaf (bytes of the block read+written), 3 gathers / copies (bytes),
+ *   4 limb splits (bytes), 5 triangular-inverse base blocks (field ops).
+ */
+long long pluq_launch_count(void);
+pluq_status pluq_profile_enable(int on);
+pluq_status pluq_profile_read(int kernel_class, long long *h_launches, double *h_ms,
+                              double *h_work);
+
 /* Number of 8-bit limbs the tensor form splits residues mod p into (1 to 4). */
 int pluq_tensor_limbs(uint32_t p);
 

@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <atomic>
+
 #include "../../include/pluq.h"
 
 namespace pluq {
@@ -125,8 +127,19 @@ struct Arena {
         if (_s != PLUQ_OK) return _s;                         \
     } while (0)
 
+// ------------------------------------------------------------ profiling --
+// Kernel classes timed by the optional profiler (see pluq_profile_read).
+namespace prof {
+enum Cls { TC_MM = 0, SIMT_MM = 1, LEAF = 2, MOVE = 3, SPLIT = 4, TRI = 5, NCLS = 6 };
+extern std::atomic<long long> g_launches;
+void start(int cls, cudaStream_t st);
+void stop(int cls, cudaStream_t st, double work);
+}  // namespace prof
+
+// Every kernel launch goes through here: error check and launch count.
 inline pluq_status last_launch()
 {
+    prof::g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError() == cudaSuccess ? PLUQ_OK : PLUQ_ECUDA;
 }
 

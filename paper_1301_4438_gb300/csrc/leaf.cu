@@ -357,8 +357,11 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
                                            (int)smem));
         attr_set = true;
     }
+    prof::start(prof::LEAF, st);
     leaf_kernel<<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q, rank);
-    return last_launch();
+    pluq_status s = last_launch();
+    prof::stop(prof::LEAF, st, (double)m * n * 8.0);
+    return s;
 }
 
 }  // namespace pluq

@@ -121,6 +121,7 @@ pluq_status launch_mm_simt(Blk C, const uint32_t *A, int64_t lda, const uint32_t
         int64_t kc = K - k0 < kchunk ? K - k0 : kchunk;
         int md = mode;
         if (k0 > 0) md = (mode == MM_ASSIGN) ? MODE_ADD : MODE_SUB;
+        prof::start(prof::SIMT_MM, st);
         if (big)
             mm_simt_kernel<true><<<grid, NT, 0, st>>>(C.ptr, C.ld, A + k0, lda, B + k0 * ldb, ldb,
                                                       (int)M, (int)N, (int)kc, F, md, sA, sB, sC);
@@ -128,6 +129,7 @@ pluq_status launch_mm_simt(Blk C, const uint32_t *A, int64_t lda, const uint32_t
             mm_simt_kernel<false><<<grid, NT, 0, st>>>(C.ptr, C.ld, A + k0, lda, B + k0 * ldb, ldb,
                                                        (int)M, (int)N, (int)kc, F, md, sA, sB, sC);
         PLUQ_TRY(last_launch());
+        prof::stop(prof::SIMT_MM, st, 2.0 * (double)M * N * kc * batch);
     }
     return PLUQ_OK;
 }

@@ -484,12 +484,14 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
     if (!pa || !pb) return PLUQ_ENOMEM;
     const uint32_t p = F.p;
     dim3 blk(32, 8);
+    prof::start(prof::SPLIT, st);
     split_rows_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32), (unsigned)batch), blk, 0,
                            st>>>(A, lda, sA, (int)M, (int)K, Mp, Kp, p, pa);
     PLUQ_TRY(last_launch());
     split_cols_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32), (unsigned)batch), blk, 0,
                            st>>>(B, ldb, sB, (int)K, (int)N, Np, Kp, p, pb);
     PLUQ_TRY(last_launch());
+    prof::stop(prof::SPLIT, st, (double)batch * ((M + N) * K * 4.0 + (Mp + Np) * Kp * 2.0 * L));
 
     CUtensorMap ma, mb;
     if (!make_map(&ma, pa, batch * L * Mp, Kp, BM)) return PLUQ_ECUDA;
@@ -517,8 +519,11 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
     a.off_hi = ((1ull << 42) / p + 1) * p;
     a.w32 = (uint32_t)((1ull << 32) % p);
     dim3 grid((unsigned)(Np / G::BN), (unsigned)(Mp / BM), (unsigned)batch);
+    prof::start(prof::TC_MM, st);
     mm_tc_kernel<L><<<grid, NTHREADS, G::SMEM, st>>>(ma, mb, a);
     PLUQ_TRY(last_launch());
+    // algorithmic tensor work: L^2 digit products of an M x K by K x N product
+    prof::stop(prof::TC_MM, st, 2.0 * L * L * (double)M * N * K * batch);
     ar.off = mark;
     return PLUQ_OK;
 }

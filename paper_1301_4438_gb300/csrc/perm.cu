@@ -147,9 +147,12 @@ pluq_status launch_gather(Blk dst, const uint32_t *src, int64_t lds, int64_t row
                           const int32_t *rmap, const int32_t *cmap, cudaStream_t st)
 {
     if (rows <= 0 || cols <= 0) return PLUQ_OK;
+    prof::start(prof::MOVE, st);
     gather_kernel<<<grid2d(rows, cols), GT, 0, st>>>(dst.ptr, dst.ld, src, lds, rows, cols, rmap,
                                                      cmap);
-    return last_launch();
+    pluq_status s = last_launch();
+    prof::stop(prof::MOVE, st, (double)rows * cols * 8.0);
+    return s;
 }
 
 pluq_status launch_copy(Blk dst, const uint32_t *src, int64_t lds, int64_t rows, int64_t cols,

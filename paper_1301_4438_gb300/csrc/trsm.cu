@@ -109,8 +109,10 @@ pluq_status tri_inv_lower_unit(const uint32_t *L, int64_t ldl, Blk X, int64_t r,
 {
     if (r <= 0) return PLUQ_OK;
     PLUQ_TRY(launch_zero(X, r, r, st));
+    prof::start(prof::TRI, st);
     inv_lower_unit_base<<<(unsigned)ceil_div(r, TB), TB, 0, st>>>(L, ldl, X.ptr, X.ld, (int)r, F);
     PLUQ_TRY(last_launch());
+    prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;
     size_t mark = ar.off;
     uint32_t *T = (uint32_t *)ar.take((size_t)r * r * sizeof(uint32_t));
@@ -145,8 +147,10 @@ pluq_status tri_inv_upper(const uint32_t *U, int64_t ldu, Blk X, int64_t r, Fiel
 {
     if (r <= 0) return PLUQ_OK;
     PLUQ_TRY(launch_zero(X, r, r, st));
+    prof::start(prof::TRI, st);
     inv_upper_base<<<(unsigned)ceil_div(r, TB), TB, 0, st>>>(U, ldu, X.ptr, X.ld, (int)r, F);
     PLUQ_TRY(last_launch());
+    prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;
     size_t mark = ar.off;
     uint32_t *T = (uint32_t *)ar.take((size_t)r * r * sizeof(uint32_t));

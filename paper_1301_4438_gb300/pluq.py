@@ -53,6 +53,11 @@ _SIGS = {
     "pluq_perm_cols": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, ctypes.c_size_t,
                                       _vp]),
     "pluq_leaf": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_u32, _vp, _vp, _vp, _vp]),
+    "pluq_launch_count": (ctypes.c_longlong, []),
+    "pluq_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pluq_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -273,3 +278,25 @@ def pluq_leaf(A: torch.Tensor, p: int, stream=None):
     _check(load().pluq_leaf(_ptr(A), m, n, A.stride(0) if m else max(n, 1), p, _ptr(pp), _ptr(pq),
                             _ptr(rk), _stream(stream)), "pluq_leaf")
     return pp[:m], pq[:n], int(rk.item())
+
+
+PROFILE_CLASSES = {"tensor_mm": 0, "simt_mm": 1, "leaf": 2, "move": 3, "split": 4, "tri_base": 5}
+
+
+def pluq_launch_count() -> int:
+    return int(load().pluq_launch_count())
+
+
+def pluq_profile_enable(on: bool = True):
+    _check(load().pluq_profile_enable(int(on)), "pluq_profile_enable")
+
+
+def pluq_profile_read(kernel_class):
+    """(launches, device ms, algorithmic work) of one kernel class since enable."""
+    cls = PROFILE_CLASSES.get(kernel_class, kernel_class)
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0)
+    w = ctypes.c_double(0)
+    _check(load().pluq_profile_read(cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(w)),
+           "pluq_profile_read")
+    return int(n.value), float(ms.value), float(w.value)
