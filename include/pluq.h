@@ -179,6 +179,36 @@ pluq_status pluq_profile_enable(int on);
 pluq_status pluq_profile_read(int kernel_class, long long *h_launches, double *h_ms,
                               double *h_work);
 
+/*
+ * Allocation-free variant of the tensor-core pluq_modmm (the paper has no
+ * counterpart: this exists for callers that cannot allocate device memory).
+ * Some callers cannot hand the library a workspace: code running inside a
+ * CUDA graph capture, where cudaMalloc is not allowed; plug-ins living in a
+ * process whose device memory is owned by another allocator (a framework's
+ * caching allocator that has reserved the card); latency-critical loops that
+ * cannot risk an allocation failing.  This entry point computes the same
+ * C <- C - A B (assign = 0) or C <- A B (assign != 0) mod p as
+ * pluq_modmm(..., PLUQ_MM_TENSOR, ...) but keeps its limb planes in a fixed
+ * device array of PLUQ_NOALLOC_SCRATCH_BYTES that the library declares
+ * statically; it calls no cudaMalloc / cudaFree and no allocating routine.
+ *  - Limit: the product must satisfy pluq_modmm_workspace_size(M, N, K, p,
+ *    PLUQ_MM_TENSOR) <= PLUQ_NOALLOC_SCRATCH_BYTES (e.g. M = N = K = 2048 for
+ *    p < 2^16); larger products return PLUQ_ENOMEM and touch nothing.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current (cudaGetSymbolAddress) and caches it; make that first
+ *    call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind (every byte a call reads is written by that call first).  Calls
+ *    whose kernels overlap on the GPU (different streams, or several host
+ *    threads) race on it; serialise them, e.g. on one stream.
+ *  - Like pluq_modmm's tensor form it is asynchronous on `stream`, and C may
+ *    overlap A or B (both are copied into the scratch before C is written).
+ */
+#define PLUQ_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u + 8192u)
+pluq_status pluq_modmm_tensor_noalloc(uint32_t *d_C, int64_t ldc, const uint32_t *d_A,
+                                      int64_t lda, const uint32_t *d_B, int64_t ldb, int64_t M,
+                                      int64_t N, int64_t K, uint32_t p, int assign, void *stream);
+
 /* Number of 8-bit limbs the tensor form splits residues mod p into (1 to 4). */
 int pluq_tensor_limbs(uint32_t p);
 

@@ -561,3 +561,57 @@ pluq_status launch_mm_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *
 }
 
 }  // namespace pluq
+
+// ------------------------------------------------------- allocation-free --
+// Scratch of pluq_modmm_tensor_noalloc: the limb planes of A and B live in this
+// fixed array instead of a caller-provided workspace.  Every device that loads
+// the library keeps it (PLUQ_NOALLOC_SCRATCH_BYTES) until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PLUQ_NOALLOC_SCRATCH_BYTES];
+
+#include <mutex>
+
+namespace pluq {
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int MAX_DEVICES = 256;
+void *g_noalloc_addr[MAX_DEVICES] = {};   // device address of the array, per device ordinal
+}  // namespace
+}  // namespace pluq
+
+extern "C" pluq_status pluq_modmm_tensor_noalloc(uint32_t *d_C, int64_t ldc, const uint32_t *d_A,
+                                                 int64_t lda, const uint32_t *d_B, int64_t ldb,
+                                                 int64_t M, int64_t N, int64_t K, uint32_t p,
+                                                 int assign, void *stream)
+{
+    using namespace pluq;
+    if (M < 0 || N < 0 || K < 0) return PLUQ_EINVAL;
+    if (p < 2 || p >= 0x80000000u) return PLUQ_ENOTPRIME;
+    for (uint64_t d = 2; d * d <= p; ++d)
+        if (p % d == 0) return PLUQ_ENOTPRIME;
+    if (M > 0 && N > 0 && (!d_C || ldc < N)) return PLUQ_EINVAL;
+    if (M > 0 && K > 0 && (!d_A || lda < K)) return PLUQ_EINVAL;
+    if (K > 0 && N > 0 && (!d_B || ldb < N)) return PLUQ_EINVAL;
+    if (mm_tc_workspace(M, N, K, p, 1) > (size_t)PLUQ_NOALLOC_SCRATCH_BYTES) return PLUQ_ENOMEM;
+
+    // set-up once per device, with that device current: the host-side name of
+    // the array is not a device address, so look the address up and keep it
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return PLUQ_ECUDA;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+                return PLUQ_ECUDA;
+            g_noalloc_addr[dev] = ptr;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    Arena ar;
+    ar.base = (char *)base;
+    ar.size = PLUQ_NOALLOC_SCRATCH_BYTES;
+    ar.off = 0;
+    return launch_mm_tc(Blk{d_C, ldc}, d_A, lda, d_B, ldb, M, N, K, make_field(p),
+                        assign ? MM_ASSIGN : MM_SUB, 1, 0, 0, 0, ar, (cudaStream_t)stream);
+}

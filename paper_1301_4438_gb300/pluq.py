@@ -53,6 +53,8 @@ _SIGS = {
     "pluq_perm_cols": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, ctypes.c_size_t,
                                       _vp]),
     "pluq_leaf": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_u32, _vp, _vp, _vp, _vp]),
+    "pluq_modmm_tensor_noalloc": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _c_i64,
+                                                 _c_i64, _c_i64, _c_u32, ctypes.c_int, _vp]),
     "pluq_launch_count": (ctypes.c_longlong, []),
     "pluq_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pluq_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
