@@ -62,6 +62,20 @@ __device__ __forceinline__ uint32_t mul_sub_mul_mod(uint32_t a, uint32_t b, uint
     return reduce64(x, F);
 }
 
+// p <= 2^16: every product of two residues fits 32 bits.  Barrett with
+// mu = floor((2^32 - 1) / p): q = hi32(x mu) > x/p - 2, so q >= floor(x/p) - 1
+// and x - q p lies in [0, 2p).
+struct Field32 {
+    uint32_t p, mu;
+};
+inline Field32 make_field32(uint32_t p) { return Field32{p, 0xFFFFFFFFu / p}; }
+
+__device__ __forceinline__ uint32_t reduce32(uint32_t x, const Field32 &F)
+{
+    uint32_t r = x - __umulhi(x, F.mu) * F.p;
+    return r >= F.p ? r - F.p : r;
+}
+
 // Inverse of a nonzero residue by the extended Euclidean algorithm.
 __device__ __forceinline__ uint32_t inv_mod(uint32_t a, uint32_t p)
 {
@@ -166,6 +180,9 @@ pluq_status launch_mm_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *
                          int64_t batch, int64_t sA, int64_t sB, int64_t sC, Arena &ar,
                          cudaStream_t st);
 size_t mm_tc_workspace(int64_t M, int64_t N, int64_t K, uint32_t p, int64_t batch);
+// Nonzero if a tensor-core kernel gave up on a bounded wait since the last
+// call (reads and clears the device word).
+int tc_error_flag();
 
 // Dispatch on the kind (SIMT needs C disjoint from A and B).
 pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uint32_t *B,
@@ -196,7 +213,15 @@ pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st);
 
 // Leaf (base case) of the recursion.
 constexpr int LEAF_MAX = 128;
+// info[0] = r, info[1] = (P is the identity), info[2] = (Q is the identity);
+// when host_info is given (mapped pinned memory) the same three words go to
+// host_info[1..3] and then seq to host_info[0].
 pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
-                        int32_t *perm_p, int32_t *perm_q, int32_t *rank, cudaStream_t st);
+                        int32_t *perm_p, int32_t *perm_q, int32_t *info, int info_len,
+                        cudaStream_t st, volatile int32_t *host_info = nullptr, int32_t seq = 0);
+
+// Products below this many multiply-adds go to the CUDA-core kernel when C
+// does not overlap A or B (launch latency dominates there).
+constexpr double SMALL_MM_MACS = 1 << 25;
 
 }  // namespace pluq

@@ -8,6 +8,7 @@
 // a block go through a scratch copy.
 #include <mutex>
 #include <new>
+#include <stdlib.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -26,13 +27,35 @@ pluq_status launch_rank_sort(const int32_t *key, const int32_t *val, int64_t r, 
 pluq_status launch_check_range(const uint32_t *A, int64_t lda, int64_t m, int64_t n, uint32_t p,
                                int32_t *flag, cudaStream_t st);
 
+namespace {
+// byte ranges [lo, hi) spanned by a batch of strided blocks
+struct Span {
+    uintptr_t lo, hi;
+};
+Span span(const uint32_t *X, int64_t ld, int64_t rows, int64_t cols, int64_t batch, int64_t stride)
+{
+    uintptr_t lo = (uintptr_t)X;
+    uintptr_t hi = lo + (uintptr_t)(((batch - 1) * stride + (rows - 1) * ld + cols) * 4);
+    return Span{lo, hi};
+}
+bool overlap(Span a, Span b) { return a.lo < b.hi && b.lo < a.hi; }
+}  // namespace
+
 pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uint32_t *B,
                       int64_t ldb, int64_t M, int64_t N, int64_t K, Field F, int mode,
                       int64_t batch, int64_t sA, int64_t sB, int64_t sC, Arena &ar,
                       cudaStream_t st)
 {
+    if (M <= 0 || N <= 0 || batch <= 0) return PLUQ_OK;
     if (kind == PLUQ_MM_SIMT)
         return launch_mm_simt(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, st);
+    // small products: one CUDA-core launch beats split + split + tensor launch,
+    // as long as C is disjoint from the operands it would overwrite
+    if (K > 0 && (double)M * N * K * batch <= SMALL_MM_MACS) {
+        Span sc = span(C.ptr, C.ld, M, N, batch, sC);
+        if (!overlap(sc, span(A, lda, M, K, batch, sA)) && !overlap(sc, span(B, ldb, K, N, batch, sB)))
+            return launch_mm_simt(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, st);
+    }
     return launch_mm_tc(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, ar, st);
 }
 
@@ -46,14 +69,42 @@ bool is_prime_u32(uint32_t p)
     return true;
 }
 
-// Pinned host word for rank read-back (one per host thread).
-int32_t *pinned_word()
+// Mapped pinned host words (one block per host thread): the leaf kernel
+// writes its rank and identity flags there and then a sequence number, and
+// the host polls the sequence number instead of copying and synchronising.
+struct HostWords {
+    volatile int32_t *h = nullptr;   // host view
+    int32_t *d = nullptr;            // device view
+    int32_t seq = 0;
+};
+HostWords *host_words()
 {
-    thread_local int32_t *w = nullptr;
-    if (!w) {
-        if (cudaHostAlloc((void **)&w, 64, cudaHostAllocDefault) != cudaSuccess) w = nullptr;
+    thread_local HostWords hw;
+    if (!hw.h) {
+        int32_t *h = nullptr;
+        if (cudaHostAlloc((void **)&h, 256, cudaHostAllocMapped | cudaHostAllocPortable) !=
+            cudaSuccess)
+            return nullptr;
+        int32_t *d = nullptr;
+        if (cudaHostGetDevicePointer((void **)&d, h, 0) != cudaSuccess) return nullptr;
+        for (int i = 0; i < 64; ++i) h[i] = 0;
+        hw.h = h;
+        hw.d = d;
     }
-    return w;
+    return &hw;
+}
+
+// wait for the leaf kernel to publish sequence number `seq` (bounded)
+pluq_status wait_words(HostWords *hw, int32_t seq, cudaStream_t st)
+{
+    for (long long it = 0;; ++it) {
+        if (hw->h[0] == seq) return PLUQ_OK;
+        if ((it & 0xFFFF) == 0xFFFF) {
+            cudaError_t e = cudaStreamQuery(st);
+            if (e == cudaSuccess) return hw->h[0] == seq ? PLUQ_OK : PLUQ_EINTERNAL;
+            if (e != cudaErrorNotReady) return PLUQ_ECUDA;
+        }
+    }
 }
 
 struct Ctx {
@@ -66,9 +117,30 @@ struct Ctx {
     int32_t *smap, *tmap; // S and T index maps of the current node
     int32_t *vstack;      // child permutation vectors (stack discipline)
     size_t vtop, vcap;
-    int32_t *d_rank;
-    int32_t *h_rank;
+    int32_t *d_rank;      // device words: range check flag, leaf info
+    HostWords *hw;
+    int64_t leaf = 64;    // blocks with both sides <= leaf go to the leaf kernel
     int64_t leaves = 0;
+};
+
+// Leaf size of the recursion: PLUQ_LEAF (16..128) if set, else 64.  Smaller
+// leaves mean less one-SM elimination work per leaf (b^3/3 per leaf, n b^2/3
+// in all for an n x n full-rank matrix) but more recursion nodes.
+int64_t leaf_size()
+{
+    const char *e = getenv("PLUQ_LEAF");
+    if (e) {
+        long v = strtol(e, nullptr, 10);
+        if (v >= 16 && v <= LEAF_MAX) return v;
+    }
+    return 64;
+}
+
+// result of a (sub)decomposition: rank, and whether P / Q are identities
+// (then their vectors are not needed by the parent and may be left unwritten)
+struct Res {
+    int64_t r = 0;
+    bool pid = true, qid = true;
 };
 
 int32_t *vtake(Ctx &c, int64_t len)
@@ -91,23 +163,37 @@ pluq_status permute_block(Ctx &c, uint32_t *X, int64_t ldx, int64_t rows, int64_
     return launch_copy(Blk{X, ldx}, c.gather, cols, rows, cols, c.st);
 }
 
-pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t *pp,
-                int32_t *pq, int64_t &r)
+// True when the (start, length) segments, taken in turn, walk 0, 1, 2, ...:
+// the block permutation S or T is then the identity.
+bool in_order(const int64_t (*seg)[2], int count)
 {
-    r = 0;
-    if (m == 0 || n == 0) {
-        PLUQ_TRY(launch_iota(pp, m, c.st));
-        PLUQ_TRY(launch_iota(pq, n, c.st));
-        return PLUQ_OK;
+    int64_t pos = 0;
+    for (int i = 0; i < count; ++i) {
+        if (seg[i][1] <= 0) continue;
+        if (seg[i][0] != pos) return false;
+        pos += seg[i][1];
     }
-    if (m <= LEAF_MAX && n <= LEAF_MAX) {
-        PLUQ_TRY(launch_leaf(A, m, n, lda, c.F, pp, pq, c.d_rank, c.st));
-        PLUQ_CUDA_TRY(cudaMemcpyAsync(c.h_rank, c.d_rank, sizeof(int32_t),
-                                      cudaMemcpyDeviceToHost, c.st));
-        PLUQ_CUDA_TRY(cudaStreamSynchronize(c.st));
-        r = *c.h_rank;
+    return true;
+}
+
+// Algorithm 1 on the m x n block at A.  On return the block holds its packed
+// factorisation; pp / pq hold P / Q unless out.pid / out.qid say they are the
+// identity (then the vectors are not written).
+pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t *pp,
+                int32_t *pq, Res &out)
+{
+    out = Res{};
+    if (m == 0 || n == 0) return PLUQ_OK;
+    if (m <= c.leaf && n <= c.leaf) {
+        const int32_t seq = ++c.hw->seq;
+        PLUQ_TRY(launch_leaf(A, m, n, lda, c.F, pp, pq, c.d_rank + 4, 3, c.st, c.hw->d, seq));
+        PLUQ_TRY(wait_words(c.hw, seq, c.st));
+        const int32_t r = c.hw->h[1];
         ++c.leaves;
         if (r < 0 || r > m || r > n) return PLUQ_EINTERNAL;
+        out.r = r;
+        out.pid = c.hw->h[2] != 0;
+        out.qid = c.hw->h[3] != 0;
         return PLUQ_OK;
     }
     const int64_t k = m / 2, h = n / 2;
@@ -117,13 +203,15 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     if (!q4) return PLUQ_ENOMEM;
     const Field F = c.F;
     auto at = [&](int64_t i, int64_t j) { return A + i * lda + j; };
+    auto vec = [](int32_t *v, bool ident) -> int32_t * { return ident ? nullptr : v; };
 
     // A1 = P1 [L1;M1][U1 V1] Q1
-    int64_t r1;
-    PLUQ_TRY(rec(c, A, k, h, lda, p1, q1, r1));
+    Res s1;
+    PLUQ_TRY(rec(c, A, k, h, lda, p1, q1, s1));
+    const int64_t r1 = s1.r;
     // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
-    PLUQ_TRY(permute_block(c, at(0, h), lda, k, n - h, p1, nullptr));
-    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, h, nullptr, q1));
+    PLUQ_TRY(permute_block(c, at(0, h), lda, k, n - h, vec(p1, s1.pid), nullptr));
+    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, h, nullptr, vec(q1, s1.qid)));
     // D <- L1^{-1} B1 ; E <- C1 U1^{-1}
     PLUQ_TRY(trsm_left_lower_unit(A, lda, Blk{at(0, h), lda}, r1, n - h, F, c.kind, c.ar, c.st));
     PLUQ_TRY(trsm_right_upper(A, lda, Blk{at(k, 0), lda}, m - k, r1, F, c.kind, c.ar, c.st));
@@ -133,15 +221,17 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     PLUQ_TRY(launch_mm(c.kind, Blk{at(k, r1), lda}, at(k, 0), lda, at(0, r1), lda, m - k, h - r1,
                        r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
-    int64_t r2, r3;
-    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, r2));
-    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, r3));
+    Res s2, s3;
+    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2));
+    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, s3));
+    const int64_t r2 = s2.r, r3 = s3.r;
+    int32_t *P2 = vec(p2, s2.pid), *Q2 = vec(q2, s2.qid), *P3 = vec(p3, s3.pid), *Q3 = vec(q3, s3.qid);
     // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
-    PLUQ_TRY(permute_block(c, at(k, h), lda, m - k, n - h, p3, q2));
-    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, r1, p3, nullptr));
-    PLUQ_TRY(permute_block(c, at(r1, 0), lda, k - r1, r1, p2, nullptr));
-    PLUQ_TRY(permute_block(c, at(0, h), lda, r1, n - h, nullptr, q2));
-    PLUQ_TRY(permute_block(c, at(0, r1), lda, r1, h - r1, nullptr, q3));
+    PLUQ_TRY(permute_block(c, at(k, h), lda, m - k, n - h, P3, Q2));
+    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, r1, P3, nullptr));
+    PLUQ_TRY(permute_block(c, at(r1, 0), lda, k - r1, r1, P2, nullptr));
+    PLUQ_TRY(permute_block(c, at(0, h), lda, r1, n - h, nullptr, Q2));
+    PLUQ_TRY(permute_block(c, at(0, r1), lda, r1, h - r1, nullptr, Q3));
     // [I;K] <- [H1;H3] U2^{-1}
     const uint32_t *U2 = at(r1, h);
     PLUQ_TRY(trsm_right_upper(U2, lda, Blk{at(k, h), lda}, m - k, r2, F, c.kind, c.ar, c.st));
@@ -159,16 +249,29 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     PLUQ_TRY(launch_mm(c.kind, Blk{at(k + r3, h + r2), lda}, at(k + r3, r1), lda, at(k, h + r2),
                        lda, m - k - r3, n - h - r2, r3, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     // R = P4 [L4;M4][U4 V4] Q4
-    int64_t r4;
-    PLUQ_TRY(rec(c, at(k + r3, h + r2), m - k - r3, n - h - r2, lda, p4, q4, r4));
+    Res s4;
+    PLUQ_TRY(rec(c, at(k + r3, h + r2), m - k - r3, n - h - r2, lda, p4, q4, s4));
+    const int64_t r4 = s4.r;
+    int32_t *P4 = vec(p4, s4.pid), *Q4 = vec(q4, s4.qid);
     // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T
-    PLUQ_TRY(permute_block(c, at(k + r3, 0), lda, m - k - r3, h + r2, p4, nullptr));
-    PLUQ_TRY(permute_block(c, at(0, h + r2), lda, k + r3, n - h - r2, nullptr, q4));
+    PLUQ_TRY(permute_block(c, at(k + r3, 0), lda, m - k - r3, h + r2, P4, nullptr));
+    PLUQ_TRY(permute_block(c, at(0, h + r2), lda, k + r3, n - h - r2, nullptr, Q4));
     // P, Q and the block permutations S, T ; A <- S^T A T^T
-    PLUQ_TRY(launch_compose(p1, p2, p3, p4, q1, q2, q3, q4, pp, pq, c.smap, c.tmap, m, n, k, h,
-                            r1, r2, r3, r4, c.st));
-    PLUQ_TRY(permute_block(c, A, lda, m, n, c.smap, c.tmap));
-    r = r1 + r2 + r3 + r4;
+    const int64_t sseg[4][2] = {{0, r1 + r2}, {k, r3 + r4}, {r1 + r2, k - r1 - r2},
+                                {k + r3 + r4, m - k - r3 - r4}};
+    const int64_t tseg[6][2] = {{0, r1}, {h, r2}, {r1, r3}, {h + r2, r4}, {r1 + r3, h - r1 - r3},
+                                {h + r2 + r4, n - h - r2 - r4}};
+    const bool s_ident = in_order(sseg, 4), t_is_id = in_order(tseg, 6);
+    out.r = r1 + r2 + r3 + r4;
+    out.pid = s_ident && s1.pid && s2.pid && s3.pid && s4.pid;
+    out.qid = t_is_id && s1.qid && s2.qid && s3.qid && s4.qid;
+    if (!out.pid || !out.qid) {
+        PLUQ_TRY(launch_compose(vec(p1, s1.pid), P2, P3, P4, vec(q1, s1.qid), Q2, Q3, Q4, pp, pq,
+                                c.smap, c.tmap, m, n, k, h, r1, r2, r3, r4, c.st));
+    }
+    if (!s_ident || !t_is_id)
+        PLUQ_TRY(permute_block(c, A, lda, m, n, s_ident ? nullptr : c.smap,
+                               t_is_id ? nullptr : c.tmap));
     c.vtop = vmark;
     return PLUQ_OK;
 }
@@ -273,20 +376,25 @@ pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_
     c.ar.base = w;
     c.ar.size = L.arena;
     c.ar.off = 0;
-    c.h_rank = pinned_word();
-    if (!c.h_rank) return PLUQ_ECUDA;
+    c.hw = host_words();
+    if (!c.hw) return PLUQ_ECUDA;
+    c.leaf = leaf_size();
 
     // every entry must already be reduced: checked before anything is written
+    int32_t flag = 0;
     PLUQ_CUDA_TRY(cudaMemsetAsync(c.d_rank, 0, sizeof(int32_t), st));
     PLUQ_TRY(launch_check_range(d_A, lda, m, n, p, c.d_rank, st));
-    PLUQ_CUDA_TRY(cudaMemcpyAsync(c.h_rank, c.d_rank, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PLUQ_CUDA_TRY(cudaMemcpyAsync(&flag, c.d_rank, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PLUQ_CUDA_TRY(cudaStreamSynchronize(st));
-    if (*c.h_rank != 0) return PLUQ_ERANGE;
+    if (flag != 0) return PLUQ_ERANGE;
 
-    int64_t r = 0;
-    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, r));
+    Res res;
+    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res));
+    if (res.pid) PLUQ_TRY(launch_iota(d_perm_p, m, st));
+    if (res.qid) PLUQ_TRY(launch_iota(d_perm_q, n, st));
     PLUQ_CUDA_TRY(cudaStreamSynchronize(st));
-    *h_rank = r;
+    if (tc_error_flag()) return PLUQ_ETIMEOUT;
+    *h_rank = res.r;
     return PLUQ_OK;
 }
 
@@ -419,7 +527,7 @@ pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t
     if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
     if ((m > 0 && !d_perm_p) || (n > 0 && !d_perm_q)) return PLUQ_EINVAL;
     if (m > 0 && n > 0 && (!d_A || lda < n)) return PLUQ_EINVAL;
-    return launch_leaf(d_A, m, n, lda, make_field(p), d_perm_p, d_perm_q, d_rank,
+    return launch_leaf(d_A, m, n, lda, make_field(p), d_perm_p, d_perm_q, d_rank, 1,
                        (cudaStream_t)stream);
 }
 

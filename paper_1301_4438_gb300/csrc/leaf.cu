@@ -66,6 +66,14 @@ __device__ __forceinline__ Mask lowest(const Mask &a, int cnt)
 // stack (no device recursion): a frame splits its rows and columns at
 // floor(half) and visits A1, F, G, R in turn, each child returning the rows
 // and columns its pivots used.
+//
+// Shortcut: when the ones inside a frame have increasing columns in row order
+// (no two of them form a descent), Algorithm 1 meets them in row order, so the
+// frame emits them at once.  Induction on the split: with no descent, F (top
+// rows, right columns) and G (bottom rows, left columns) cannot both hold a
+// one, and A1 < F < R and A1 < G < R in row order; each quadrant is again
+// descent-free.  Generic rank profiles, and frames with at most one one, end
+// here after a single pass over their rows.
 struct Frame {
     Mask rows, cols, rt, rb, cl, cr;
     Mask r1, c1, c2, r3;
@@ -86,11 +94,46 @@ __device__ int order_pivots(Frame *stk, const int32_t *col_of_row, const int32_t
     stk[0].cols = cols;
     stk[0].stage = 0;
     Mask ret_r{{0, 0}}, ret_c{{0, 0}};   // used masks returned by the last popped frame
+    Mask prow_mask{{0, 0}};               // rows holding a one of R
+    for (int i = 0; i < m; ++i)
+        if (col_of_row[i] >= 0) set(prow_mask, i);
     while (top >= 0) {
         Frame &f = stk[top];
         if (f.stage == 0) {
             f.ur = Mask{{0, 0}};
             f.uc = Mask{{0, 0}};
+            // ones of R inside the frame, in row order: descent-free?
+            bool mono = true;
+            int lastc = -1;
+            for (int w = 0; w < 2 && mono; ++w) {
+                uint64_t bits = f.rows.w[w] & prow_mask.w[w];
+                while (bits) {
+                    const int i = 64 * w + __ffsll(bits) - 1;
+                    bits &= bits - 1;
+                    const int c = col_of_row[i];
+                    if (c >= 0 && has(f.cols, c)) {
+                        if (c < lastc) { mono = false; break; }
+                        lastc = c;
+                    }
+                }
+            }
+            if (mono) {
+                for (int w = 0; w < 2; ++w) {
+                    uint64_t bits = f.rows.w[w] & prow_mask.w[w];
+                    while (bits) {
+                        const int i = 64 * w + __ffsll(bits) - 1;
+                        bits &= bits - 1;
+                        const int c = col_of_row[i];
+                        if (c >= 0 && has(f.cols, c)) {
+                            ord_row[count] = i; ord_col[count] = c; ++count;
+                            set(f.ur, i); set(f.uc, c);
+                        }
+                    }
+                }
+                ret_r = f.ur; ret_c = f.uc;
+                --top;
+                continue;
+            }
             const int nr = popc(f.rows), nc = popc(f.cols);
             if (nr == 0 || nc == 0 || nr == 1 || nc == 1) {
                 if (nr == 1 && nc >= 1) {
@@ -149,166 +192,341 @@ __device__ int order_pivots(Frame *stk, const int32_t *col_of_row, const int32_t
 }
 
 struct LeafShared {
-    uint32_t W[LM * LD];
+    uint32_t W[LM * LD];                 // staging of the final block
+    uint32_t cand[2][NW][LM];            // per-warp candidate pivot rows (double buffered)
+    uint32_t pbuf[2][LM];                // pivot row of the reordered elimination
     int32_t piv_row[LM], piv_col[LM];
     int32_t col_of_row[LM], row_of_col[LM];
     int32_t ord_row[LM], ord_col[LM];
     int32_t perm_p[LM], perm_q[LM];
     uint32_t dval[LM], inv_d[LM], cval[LM], inv_c[LM];
-    uint32_t live[LM / 32];     // live (non-pivot) columns as a bitset
     Frame stk[MAX_DEPTH];
-    int key;
+    int key[3];
     int r;
     int same;
 };
 
-// elements of the (rows x cols) update region handled by this thread:
-// columns j = cbase + (tid % cw), rows i = rbase + tid / cw + g * (LT / cw)
-__device__ __forceinline__ int col_width(int n)
+constexpr int NOKEY = 0x7FFFFFFF;
+constexpr int MAXC = LM / 32;  // column slots per lane for the widest block
+
+// (d w - f q) mod p
+template <bool SMALLP>
+__device__ __forceinline__ uint32_t ff_update(uint32_t d, uint32_t w, uint32_t f, uint32_t q,
+                                              const Field &F, const Field32 &F32)
 {
-    int cw = 1;
-    while (cw < n) cw <<= 1;
-    return cw;  // <= LM
+    if (SMALLP) return sub_mod(reduce32(d * w, F32), reduce32(f * q, F32), F32.p);
+    return mul_sub_mul_mod(d, w, f, q, F);
 }
 
+template <bool SMALLP>
+__device__ __forceinline__ uint32_t scale(uint32_t d, uint32_t w, const Field &F, const Field32 &F32)
+{
+    if (SMALLP) return reduce32(d * w, F32);
+    return mul_mod(d, w, F);
+}
+
+template <int CPL>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&v)[CPL], int s)
+{
+    uint32_t x = v[0];
+#pragma unroll
+    for (int t = 1; t < CPL; ++t)
+        if (s == t) x = v[t];
+    return x;
+}
+
+// Block-wide helpers for 512 threads: warp 0 turns a per-row flag into the
+// positions of the flagged rows (exclusive prefix counts).
+__device__ __forceinline__ int warp_prefix_count(bool flag, int lane, int &total)
+{
+    const unsigned b = __ballot_sync(0xFFFFFFFFu, flag);
+    total = __popc(b);
+    return __popc(b & ((1u << lane) - 1u));
+}
+
+// Warp 0: exclusive prefix products c_k = d_0 ... d_{k-1} of dval[0..r).
+__device__ void prefix_products(LeafShared &S, int r, int lane, const Field &F)
+{
+    // lane owns entries 4 lane .. 4 lane + 3
+    uint32_t loc[MAXC];
+    uint32_t prod = 1;
+#pragma unroll
+    for (int t = 0; t < MAXC; ++t) {
+        const int k = MAXC * lane + t;
+        loc[t] = prod;                         // product of this lane's earlier entries
+        if (k < r) prod = mul_mod(prod, S.dval[k], F);
+    }
+    // exclusive scan of the lane products
+    uint32_t incl = prod;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl = mul_mod(incl, v, F);
+    }
+    uint32_t excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+    if (lane == 0) excl = 1;
+#pragma unroll
+    for (int t = 0; t < MAXC; ++t) {
+        const int k = MAXC * lane + t;
+        if (k < r) S.cval[k] = mul_mod(excl, loc[t], F);
+    }
+}
+
+// CPL column slots per lane (block width <= 32 CPL), RPW row slots per warp
+// (block height <= NW RPW): only slots that can hold data are compiled in.
+template <bool SMALLP, int CPL, int RPW>
 __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int m, int n,
                                                   int64_t lda, Field F, int32_t *perm_p_out,
-                                                  int32_t *perm_q_out, int32_t *rank_out)
+                                                  int32_t *perm_q_out, int32_t *info_out,
+                                                  int info_len, volatile int32_t *host_info,
+                                                  int32_t seq)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = F.p;
-    const int cw = col_width(n);
-    const int rstep = LT / cw;
-    const int my_c = tid % cw, my_r0 = tid / cw;
+    const Field32 F32{p, 0xFFFFFFFFu / p};
 
-    // load the block
-    for (int e = tid; e < m * cw; e += LT) {
-        int i = e / cw, j = e % cw;
-        if (j < n) S.W[i * LD + j] = A[(int64_t)i * lda + j];
+    // this warp's rows warp + NW t and this lane's columns lane + 32 s, in registers
+    uint32_t w[RPW][CPL];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+        const int i = warp + NW * t;
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+            const int j = lane + 32 * s;
+            w[t][s] = (i < m && j < n) ? A[(int64_t)i * lda + j] : 0u;
+        }
     }
     for (int i = tid; i < LM; i += LT) {
         S.col_of_row[i] = -1;
         S.row_of_col[i] = -1;
     }
-    if (tid < LM / 32) {
-        int lo = tid * 32;
-        int cnt = n - lo;
-        S.live[tid] = cnt >= 32 ? 0xFFFFFFFFu : (cnt <= 0 ? 0u : ((1u << cnt) - 1u));
-    }
-    if (tid == 0) S.r = 0;
+    if (tid == 0) S.key[0] = NOKEY;
+    uint32_t live = 0;   // bit s: column lane + 32 s is not a pivot column yet
+#pragma unroll
+    for (int s = 0; s < CPL; ++s)
+        if (lane + 32 * s < n) live |= 1u << s;
+    // warp-uniform loop bounds: column slots in use, row slots below m
+    const int ncl = (n + 31) / 32;
+    const int tmax = warp < m ? (m - warp + NW - 1) / NW : 0;
     __syncthreads();
 
     // ---------------- phase 1: row-order fraction-free elimination --------
-    int start = 0;
-    int r = 0;
-    while (start < m) {
-        if (tid == 0) S.key = 0x7FFFFFFF;
-        __syncthreads();
-        // each warp scans its rows in increasing order, stops at the first hit
-        for (int i = start + warp; i < m; i += NW) {
-            int best = 0x7FFFFFFF;
+    // Step t: rows below the last pivot row are updated in registers; each
+    // warp offers its first row (at or below the pivot row + 1) with a live
+    // nonzero, publishing the row itself in cand[t & 1][warp]; key[t % 3]
+    // takes the block-wide minimum (row, column).  key[(t+1) % 3] is cleared
+    // during step t: every read of it happened before the previous barrier
+    // and every write comes after the next one.
+    int r = 0, pi = -1, pc = 0, win = 0;
+    uint32_t d = 0;
+    for (int step = 0;; ++step) {
+        if (tid == 0) S.key[(step + 1) % 3] = NOKEY;
+        const int t0 = pi < warp ? 0 : (pi - warp) / NW + 1;   // first own row below pi
+        if (pi >= 0) {
+            uint32_t prow[CPL];
 #pragma unroll
-            for (int s = 0; s < LM / 32; ++s) {
-                int j = lane + 32 * s;
-                if (j < n && ((S.live[s] >> lane) & 1) && S.W[i * LD + j] != 0) {
-                    best = j < best ? j : best;
+            for (int s = 0; s < CPL; ++s)
+                if (s < ncl) prow[s] = S.cand[(step - 1) & 1][win][lane + 32 * s];
+            const int spc = pc >> 5, lpc = pc & 31;
+#pragma unroll
+            for (int t = 0; t < RPW; ++t) {
+                if (t < t0) continue;
+                if (t >= tmax) break;
+                const uint32_t f = __shfl_sync(0xFFFFFFFFu, pick<CPL>(w[t], spc), lpc);
+                if (f != 0) {
+#pragma unroll
+                    for (int s = 0; s < CPL; ++s)
+                        if (s < ncl && ((live >> s) & 1))
+                            w[t][s] = ff_update<SMALLP>(d, w[t][s], f, prow[s], F, F32);
+                } else if (d != 1) {
+#pragma unroll
+                    for (int s = 0; s < CPL; ++s)
+                        if (s < ncl && ((live >> s) & 1)) w[t][s] = scale<SMALLP>(d, w[t][s], F, F32);
                 }
             }
+        }
+        // this warp's first candidate row: OR of the lanes' row masks, then
+        // the smallest live nonzero column of that row
+        unsigned rows_nz = 0;
+#pragma unroll
+        for (int t = 0; t < RPW; ++t) {
+            if (t < t0) continue;
+            if (t >= tmax) break;
+            bool nz = false;
+#pragma unroll
+            for (int s = 0; s < CPL; ++s)
+                if (s < ncl) nz |= ((live >> s) & 1) && w[t][s] != 0;
+            rows_nz |= (unsigned)nz << t;
+        }
+        rows_nz = __reduce_or_sync(0xFFFFFFFFu, rows_nz);
+        if (rows_nz) {
+            const int ct = __ffs(rows_nz) - 1;
+            int best = NOKEY;
+#pragma unroll
+            for (int t = 0; t < RPW; ++t)
+                if (t == ct) {
+#pragma unroll
+                    for (int s = CPL - 1; s >= 0; --s)
+                        if (s < ncl && ((live >> s) & 1) && w[t][s] != 0) best = lane + 32 * s;
+#pragma unroll
+                    for (int s = 0; s < CPL; ++s)
+                        if (s < ncl) S.cand[step & 1][warp][lane + 32 * s] = w[t][s];
+                }
             best = __reduce_min_sync(0xFFFFFFFFu, best);
-            if (best != 0x7FFFFFFF) {
-                if (lane == 0) atomicMin(&S.key, i * LM + best);
-                break;
-            }
-            // rows beyond the current best need not be scanned (warp-uniform test)
-            const int cur = __shfl_sync(0xFFFFFFFFu, *(volatile int *)&S.key, 0);
-            if (cur < (i + NW) * LM) break;
+            if (lane == 0) atomicMin(&S.key[step % 3], (warp + NW * ct) * LM + best);
         }
         __syncthreads();
-        const int key = S.key;
-        if (key == 0x7FFFFFFF) break;
-        const int pi = key / LM, pc = key % LM;
-        const uint32_t d = S.W[pi * LD + pc];
+        const int kv = S.key[step % 3];
+        if (kv == NOKEY) break;
+        pi = kv / LM;
+        pc = kv % LM;
+        win = pi % NW;
+        d = S.cand[step & 1][win][pc];
+        if ((pc & 31) == lane) live &= ~(1u << (pc >> 5));
         if (tid == 0) {
             S.piv_row[r] = pi;
             S.piv_col[r] = pc;
             S.dval[r] = d;
             S.col_of_row[pi] = pc;
             S.row_of_col[pc] = pi;
-            S.live[pc >> 5] &= ~(1u << (pc & 31));
-        }
-        __syncthreads();   // live updated; column pc now frozen
-        // rows below the pivot row: W[i][j] = d W[i][j] - W[i][pc] W[pi][j], live j
-        if (my_c < n && ((S.live[my_c >> 5] >> (my_c & 31)) & 1)) {
-            const uint32_t prow = S.W[pi * LD + my_c];
-            for (int i = pi + 1 + my_r0; i < m; i += rstep) {
-                uint32_t f = S.W[i * LD + pc];
-                uint32_t *w = &S.W[i * LD + my_c];
-                *w = mul_sub_mul_mod(d, *w, f, prow, F);
-            }
         }
         ++r;
-        start = pi + 1;
-        __syncthreads();
     }
 
     // ---------------- phase 2: Algorithm 1's order of the pivots ----------
-    if (tid == 0) {
-        const int cnt = order_pivots(S.stk, S.col_of_row, S.row_of_col, m, n, S.ord_row, S.ord_col);
-        int same = cnt == r ? 1 : -1;   // -1: inconsistent, reported as an error
-        if (same < 0) r = 0;
-        for (int t = 0; t < r; ++t)
-            if (S.ord_row[t] != S.piv_row[t]) same = 0;
-        // P, Q: pivots in order, then the others increasing
-        int a = 0;
-        for (int t = 0; t < r; ++t) S.perm_p[a++] = S.ord_row[t];
-        for (int i = 0; i < m; ++i)
-            if (S.col_of_row[i] < 0) S.perm_p[a++] = i;
-        a = 0;
-        for (int t = 0; t < r; ++t) S.perm_q[a++] = S.ord_col[t];
-        for (int j = 0; j < n; ++j)
-            if (S.row_of_col[j] < 0) S.perm_q[a++] = j;
-        S.same = same;
-        S.r = r;
+    // Pivots whose columns increase in row order are already in that order
+    // (see order_pivots); otherwise thread 0 runs the quad recursion.
+    bool descent = false;
+    for (int t = tid; t + 1 < r; t += LT) descent |= S.piv_col[t] > S.piv_col[t + 1];
+    descent = __syncthreads_or(descent);
+    if (descent) {
+        if (tid == 0) {
+            const int cnt = order_pivots(S.stk, S.col_of_row, S.row_of_col, m, n, S.ord_row, S.ord_col);
+            int same = cnt == r ? 1 : -1;
+            if (same > 0)
+                for (int t = 0; t < r; ++t)
+                    if (S.ord_row[t] != S.piv_row[t]) same = 0;
+            S.same = same;
+        }
+    } else {
+        for (int t = tid; t < r; t += LT) {
+            S.ord_row[t] = S.piv_row[t];
+            S.ord_col[t] = S.piv_col[t];
+        }
+        if (tid == 0) S.same = 1;
     }
     __syncthreads();
     const int same = S.same;
     if (same < 0) {                 // leave the block untouched, flag the error
-        if (tid == 0) *rank_out = -1;
+        if (tid == 0) {
+            info_out[0] = -1;
+            if (host_info) {
+                host_info[1] = -1;
+                __threadfence_system();
+                host_info[0] = seq;
+            }
+        }
         return;
     }
+    // P, Q: pivots in order, then the other rows / columns increasing
+    for (int t = tid; t < r; t += LT) {
+        S.perm_p[t] = S.ord_row[t];
+        S.perm_q[t] = S.ord_col[t];
+    }
+    if (warp == 0) {
+        int base = 0;
+        for (int c0 = 0; c0 < m; c0 += 32) {
+            const int i = c0 + lane;
+            const bool np = i < m && S.col_of_row[i] < 0;
+            int tot;
+            const int pos = warp_prefix_count(np, lane, tot);
+            if (np) S.perm_p[r + base + pos] = i;
+            base += tot;
+        }
+    } else if (warp == 1) {
+        int base = 0;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int j = c0 + lane;
+            const bool np = j < n && S.row_of_col[j] < 0;
+            int tot;
+            const int pos = warp_prefix_count(np, lane, tot);
+            if (np) S.perm_q[r + base + pos] = j;
+            base += tot;
+        }
+    }
+    __syncthreads();
+    int pid = 1, qid = 1;
+    for (int i = tid; i < m; i += LT) pid &= S.perm_p[i] == i;
+    for (int j = tid; j < n; j += LT) qid &= S.perm_q[j] == j;
+    pid = __syncthreads_and(pid);
+    qid = __syncthreads_and(qid);
 
     // ---------------- phase 3: elimination without pivoting ---------------
     if (!same) {
-        for (int e = tid; e < m * cw; e += LT) {
-            int i = e / cw, j = e % cw;
-            if (j < n) S.W[i * LD + j] = A[(int64_t)S.perm_p[i] * lda + S.perm_q[j]];
+        // row i of P^T A Q^T in registers (rows warp + NW t, columns lane + 32 s)
+#pragma unroll
+        for (int t = 0; t < RPW; ++t) {
+            const int i = warp + NW * t;
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                const int j = lane + 32 * s;
+                w[t][s] = (i < m && j < n) ? A[(int64_t)S.perm_p[i] * lda + S.perm_q[j]] : 0u;
+            }
+        }
+        if (warp == 0) {
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) S.pbuf[0][lane + 32 * s] = w[0][s];
         }
         __syncthreads();
         for (int k = 0; k < r; ++k) {
-            const uint32_t d = S.W[k * LD + k];
-            if (tid == 0) S.dval[k] = d;
-            if (my_c > k && my_c < n) {
-                const uint32_t prow = S.W[k * LD + my_c];
-                for (int i = k + 1 + my_r0; i < m; i += rstep) {
-                    uint32_t f = S.W[i * LD + k];
-                    uint32_t *w = &S.W[i * LD + my_c];
-                    *w = mul_sub_mul_mod(d, *w, f, prow, F);
+            uint32_t prow[CPL];
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) prow[s] = S.pbuf[k & 1][lane + 32 * s];
+            const uint32_t dk = S.pbuf[k & 1][k];
+            if (tid == 0) S.dval[k] = dk;
+            const int sk = k >> 5, lk = k & 31;
+            const int tk = k < warp ? 0 : (k - warp) / NW + 1;   // first own row below k
+#pragma unroll
+            for (int t = 0; t < RPW; ++t) {
+                if (t < tk) continue;
+                if (t >= tmax) break;
+                const uint32_t f = __shfl_sync(0xFFFFFFFFu, pick<CPL>(w[t], sk), lk);
+#pragma unroll
+                for (int s = 0; s < CPL; ++s) {
+                    const int j = lane + 32 * s;
+                    if (s < ncl && j > k && j < n)
+                        w[t][s] = ff_update<SMALLP>(dk, w[t][s], f, prow[s], F, F32);
                 }
+            }
+            // the owner of row k + 1 publishes it for the next step
+            const int nk = k + 1;
+            if (nk < m && warp == nk % NW) {
+#pragma unroll
+                for (int t = 0; t < RPW; ++t)
+                    if (warp + NW * t == nk) {
+#pragma unroll
+                        for (int s = 0; s < CPL; ++s) S.pbuf[nk & 1][lane + 32 * s] = w[t][s];
+                    }
             }
             __syncthreads();
         }
     }
 
-    // ---------------- fix-up: divide U rows by c_k, L columns by d_k ------
-    if (tid == 0) {
-        uint32_t c = 1;
-        for (int k = 0; k < r; ++k) {
-            S.cval[k] = c;
-            c = mul_mod(c, S.dval[k], F);
+    // stage the rows in shared memory (original positions after phase 1,
+    // P^T A Q^T positions after phase 3)
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+        const int i = warp + NW * t;
+        if (i < m) {
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) S.W[i * LD + lane + 32 * s] = w[t][s];
         }
     }
+    // ---------------- fix-up: divide U rows by c_k, L columns by d_k ------
+    __syncthreads();
+    if (warp == 0) prefix_products(S, r, lane, F);
     __syncthreads();
     for (int t = tid; t < 2 * r; t += LT) {
         if (t < r) S.inv_d[t] = inv_mod(S.dval[t], p);
@@ -317,16 +535,16 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     __syncthreads();
 
     // write the packed block [L\U V; M 0] in P, Q order
-    for (int e = tid; e < m * cw; e += LT) {
-        int i = e / cw, j = e % cw;
+    for (int e = tid; e < m * LM; e += LT) {
+        const int i = e / LM, j = e % LM;
         if (j >= n) continue;
         uint32_t v;
         if (i < r && j >= i) {
-            uint32_t w = same ? S.W[S.piv_row[i] * LD + S.perm_q[j]] : S.W[i * LD + j];
-            v = mul_mod(w, S.inv_c[i], F);
+            uint32_t x = same ? S.W[S.piv_row[i] * LD + S.perm_q[j]] : S.W[i * LD + j];
+            v = mul_mod(x, S.inv_c[i], F);
         } else if (j < r && i > j) {
-            uint32_t w = same ? S.W[S.perm_p[i] * LD + S.piv_col[j]] : S.W[i * LD + j];
-            v = mul_mod(w, S.inv_d[j], F);
+            uint32_t x = same ? S.W[S.perm_p[i] * LD + S.piv_col[j]] : S.W[i * LD + j];
+            v = mul_mod(x, S.inv_d[j], F);
         } else {
             v = 0;
         }
@@ -334,31 +552,63 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     }
     for (int i = tid; i < m; i += LT) perm_p_out[i] = S.perm_p[i];
     for (int j = tid; j < n; j += LT) perm_q_out[j] = S.perm_q[j];
-    if (tid == 0) *rank_out = r;
+    if (tid == 0) {
+        info_out[0] = r;
+        if (info_len > 2) {
+            info_out[1] = pid;
+            info_out[2] = qid;
+        }
+        if (host_info) {
+            host_info[1] = r;
+            host_info[2] = pid;
+            host_info[3] = qid;
+            __threadfence_system();
+            host_info[0] = seq;
+        }
+    }
 }
 
 }  // namespace
 
 pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F, int32_t *perm_p,
-                        int32_t *perm_q, int32_t *rank, cudaStream_t st)
+                        int32_t *perm_q, int32_t *info, int info_len, cudaStream_t st,
+                        volatile int32_t *host_info, int32_t seq)
 {
     if (m < 0 || n < 0 || m > LM || n > LM) return PLUQ_EINVAL;
     if (m == 0 || n == 0) {
         // empty block: r = 0, identity permutations
         if (m) PLUQ_TRY(launch_iota(perm_p, m, st));
         if (n) PLUQ_TRY(launch_iota(perm_q, n, st));
-        PLUQ_CUDA_TRY(cudaMemsetAsync(rank, 0, sizeof(int32_t), st));
+        PLUQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t), st));
         return PLUQ_OK;
     }
-    static bool attr_set = false;
     const size_t smem = sizeof(LeafShared);
-    if (!attr_set) {
-        PLUQ_CUDA_TRY(cudaFuncSetAttribute(leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        attr_set = true;
-    }
+    const int cpl = n <= 32 ? 1 : n <= 64 ? 2 : 4;
+    const int rpw = m <= 32 ? 2 : m <= 64 ? 4 : 8;
+    const bool small = F.p <= 65536u;
     prof::start(prof::LEAF, st);
-    leaf_kernel<<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q, rank);
+    pluq_status ls = PLUQ_OK;
+#define PLUQ_LEAF_CASE(SP, C, R)                                                                  \
+    if (small == SP && cpl == C && rpw == R) {                                                   \
+        static bool attr = false;                                                                \
+        if (!attr) {                                                                             \
+            if (cudaFuncSetAttribute(leaf_kernel<SP, C, R>,                                      \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=  \
+                cudaSuccess)                                                                     \
+                return PLUQ_ECUDA;                                                               \
+            attr = true;                                                                         \
+        }                                                                                        \
+        leaf_kernel<SP, C, R><<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q,    \
+                                                   info, info_len, host_info, seq);              \
+    }
+    PLUQ_LEAF_CASE(true, 1, 2) PLUQ_LEAF_CASE(true, 1, 4) PLUQ_LEAF_CASE(true, 1, 8)
+    PLUQ_LEAF_CASE(true, 2, 2) PLUQ_LEAF_CASE(true, 2, 4) PLUQ_LEAF_CASE(true, 2, 8)
+    PLUQ_LEAF_CASE(true, 4, 2) PLUQ_LEAF_CASE(true, 4, 4) PLUQ_LEAF_CASE(true, 4, 8)
+    PLUQ_LEAF_CASE(false, 1, 2) PLUQ_LEAF_CASE(false, 1, 4) PLUQ_LEAF_CASE(false, 1, 8)
+    PLUQ_LEAF_CASE(false, 2, 2) PLUQ_LEAF_CASE(false, 2, 4) PLUQ_LEAF_CASE(false, 2, 8)
+    PLUQ_LEAF_CASE(false, 4, 2) PLUQ_LEAF_CASE(false, 4, 4) PLUQ_LEAF_CASE(false, 4, 8)
+#undef PLUQ_LEAF_CASE
+    (void)ls;
     pluq_status s = last_launch();
     prof::stop(prof::LEAF, st, (double)m * n * 8.0);
     return s;

@@ -530,6 +530,14 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
 
 }  // namespace
 
+int tc_error_flag()
+{
+    int v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+    return v;
+}
+
 size_t mm_tc_workspace(int64_t M, int64_t N, int64_t K, uint32_t p, int64_t batch)
 {
     const int L = limbs_for_prime(p);

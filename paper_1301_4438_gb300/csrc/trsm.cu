@@ -3,103 +3,152 @@
 //
 // Instead of a substitution whose critical path is one column of B per step,
 // the triangle is inverted first and the solve becomes one modular product:
-//   - 64 x 64 diagonal blocks are inverted by substitution, one thread block
+//   - 32 x 32 diagonal blocks are inverted by substitution, one thread block
 //     per diagonal block, all blocks in one launch;
-//   - blocks are then merged pairwise, log2(r/64) levels, with
+//   - blocks are then merged pairwise, log2(r/32) levels, with
 //       [L11 0; L21 L22]^-1 = [X11 0; -X22 L21 X11  X22],
 //       [U11 U12; 0 U22]^-1 = [X11 -X11 U12 X22; 0 X22],
 //     every pair of a level in one batched product launch;
 //   - the solve is X B (or B X).
 // The inverse costs r^3/3 field operations, small next to the r^2 N of the
 // solve for the shapes Algorithm 1 produces, and the launches per TRSM drop
-// from O(r/64) to O(log(r/64)).
+// from O(r/32) to O(log(r/32)).
 #include "common.cuh"
 
 namespace pluq {
 namespace {
 
-constexpr int TB = 64;
+constexpr int TB = 32;
 
-// Sum of up to 2^17 products a_l * b_l (a, b < 2^31) held exactly in two
-// 64-bit words: a = a_hi 2^16 + a_lo.
+// Sum of up to 2^17 products a_l * b_l (a, b < 2^31) held exactly in 64-bit
+// words.  p <= 2^16: one word (products < 2^32).  Otherwise a = a_hi 2^16 +
+// a_lo and two words; w16 = 2^16 mod p recombines them.
+template <bool SMALLP>
 struct Acc {
     uint64_t lo = 0, hi = 0;
     __device__ __forceinline__ void add(uint32_t a, uint32_t b)
     {
-        lo += (uint64_t)(a & 0xFFFFu) * b;
-        hi += (uint64_t)(a >> 16) * b;
+        if (SMALLP) {
+            lo += (uint64_t)(a * b);
+        } else {
+            lo += (uint64_t)(a & 0xFFFFu) * b;
+            hi += (uint64_t)(a >> 16) * b;
+        }
     }
-    __device__ __forceinline__ uint32_t value(const Field &F) const
+    __device__ __forceinline__ uint32_t value(const Field &F, uint32_t w16) const
     {
-        uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+        if (SMALLP) return reduce64(lo, F);
         return add_mod(reduce64(lo, F), mul_mod(reduce64(hi, F), w16, F), F.p);
     }
 };
 
-// X_b = (diagonal block b of L)^-1, unit lower.  One block of TB threads per
-// diagonal block; thread j owns column j of X.
-__global__ void inv_lower_unit_base(const uint32_t *__restrict__ L, int64_t ldl,
-                                    uint32_t *__restrict__ X, int64_t ldx, int r, Field F)
+// Diagonal-block inverses, one 128-thread block per TB x TB diagonal block.
+// Thread (g, j) owns column j and the rows i = g, g + RG, ..., and keeps the
+// running sums of its entries in registers; X is produced row by row (one
+// barrier per row), each finished row feeding the sums of the rows after it.
+constexpr int BT = 128, RG = BT / TB, RPT = TB / RG;   // row groups, rows per thread
+
+// X_b = (diagonal block b of L)^-1, L unit lower:
+// X[i][j] = -sum_{j <= l < i} L[i][l] X[l][j] for i > j, X[j][j] = 1.
+template <bool SMALLP>
+__global__ void __launch_bounds__(BT) inv_lower_unit_base(const uint32_t *__restrict__ L,
+                                                          int64_t ldl, uint32_t *__restrict__ X,
+                                                          int64_t ldx, int r, Field F)
 {
     __shared__ uint32_t Ls[TB][TB + 1];
     __shared__ uint32_t Xs[TB][TB + 1];
-    const int b = blockIdx.x, o = b * TB;
+    const int o = blockIdx.x * TB;
     const int sb = min(TB, r - o);
-    const int j = threadIdx.x;
-    for (int i = 0; i < sb; ++i)
-        if (j < sb) Ls[i][j] = L[(int64_t)(o + i) * ldl + o + j];
+    const int j = threadIdx.x % TB, g = threadIdx.x / TB;
+    for (int e = threadIdx.x; e < TB * TB; e += BT) {
+        const int i = e / TB, c = e % TB;
+        Ls[i][c] = (i < sb && c < sb) ? L[(int64_t)(o + i) * ldl + o + c] : 0u;
+    }
+    Acc<SMALLP> acc[RPT];
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
     __syncthreads();
-    if (j < sb) {
-        for (int i = 0; i < sb; ++i) {
+    for (int l = 0; l < sb; ++l) {
+        if (l % RG == g) {
             uint32_t v;
-            if (i < j) v = 0;
-            else if (i == j) v = 1;
+            if (l < j) v = 0;
+            else if (l == j) v = 1;
             else {
-                Acc acc;
-                for (int l = j; l < i; ++l) acc.add(Ls[i][l], Xs[l][j]);
-                uint32_t s = acc.value(F);
+                uint32_t s = 0;
+#pragma unroll
+                for (int t = 0; t < RPT; ++t)
+                    if (g + RG * t == l) s = acc[t].value(F, w16);
                 v = s == 0 ? 0 : F.p - s;
             }
-            Xs[i][j] = v;
+            Xs[l][j] = v;
+        }
+        __syncthreads();
+        const uint32_t xl = Xs[l][j];
+        if (xl != 0) {
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                const int i = g + RG * t;
+                if (i > l) acc[t].add(Ls[i][l], xl);
+            }
         }
     }
     __syncthreads();
-    for (int i = 0; i < sb; ++i)
-        if (j < sb) X[(int64_t)(o + i) * ldx + o + j] = Xs[i][j];
+    for (int e = threadIdx.x; e < sb * sb; e += BT) {
+        const int i = e / sb, c = e % sb;
+        X[(int64_t)(o + i) * ldx + o + c] = Xs[i][c];
+    }
 }
 
-// X_b = (diagonal block b of U)^-1, upper.
-__global__ void inv_upper_base(const uint32_t *__restrict__ U, int64_t ldu,
-                               uint32_t *__restrict__ X, int64_t ldx, int r, Field F)
+// X_b = (diagonal block b of U)^-1, U upper with nonzero diagonal:
+// X[i][j] = U[i][i]^-1 (delta_ij - sum_{i < l <= j} U[i][l] X[l][j]), rows bottom-up.
+template <bool SMALLP>
+__global__ void __launch_bounds__(BT) inv_upper_base(const uint32_t *__restrict__ U, int64_t ldu,
+                                                     uint32_t *__restrict__ X, int64_t ldx, int r,
+                                                     Field F)
 {
     __shared__ uint32_t Us[TB][TB + 1];
     __shared__ uint32_t Xs[TB][TB + 1];
     __shared__ uint32_t dinv[TB];
-    const int b = blockIdx.x, o = b * TB;
+    const int o = blockIdx.x * TB;
     const int sb = min(TB, r - o);
-    const int j = threadIdx.x;
-    for (int i = 0; i < sb; ++i)
-        if (j < sb) Us[i][j] = U[(int64_t)(o + i) * ldu + o + j];
+    const int j = threadIdx.x % TB, g = threadIdx.x / TB;
+    for (int e = threadIdx.x; e < TB * TB; e += BT) {
+        const int i = e / TB, c = e % TB;
+        Us[i][c] = (i < sb && c < sb) ? U[(int64_t)(o + i) * ldu + o + c] : 0u;
+    }
     __syncthreads();
-    if (j < sb) dinv[j] = inv_mod(Us[j][j], F.p);
+    if (threadIdx.x < sb) dinv[threadIdx.x] = inv_mod(Us[threadIdx.x][threadIdx.x], F.p);
+    Acc<SMALLP> acc[RPT];
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
     __syncthreads();
-    if (j < sb) {
-        for (int i = sb - 1; i >= 0; --i) {
+    for (int l = sb - 1; l >= 0; --l) {
+        if (l % RG == g) {
             uint32_t v;
-            if (i > j) v = 0;
-            else if (i == j) v = dinv[j];
+            if (l > j) v = 0;
             else {
-                Acc acc;
-                for (int l = i + 1; l <= j; ++l) acc.add(Us[i][l], Xs[l][j]);
-                uint32_t s = mul_mod(acc.value(F), dinv[i], F);
-                v = s == 0 ? 0 : F.p - s;
+                uint32_t s = 0;                              // sum_{l < t <= j} U[l][t] X[t][j]
+#pragma unroll
+                for (int t = 0; t < RPT; ++t)
+                    if (g + RG * t == l) s = acc[t].value(F, w16);
+                uint32_t rhs = (l == j) ? 1u : 0u;
+                v = mul_mod(sub_mod(rhs, s, F.p), dinv[l], F);
             }
-            Xs[i][j] = v;
+            Xs[l][j] = v;
+        }
+        __syncthreads();
+        const uint32_t xl = Xs[l][j];
+        if (xl != 0) {
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                const int i = g + RG * t;
+                if (i < l) acc[t].add(Us[i][l], xl);
+            }
         }
     }
     __syncthreads();
-    for (int i = 0; i < sb; ++i)
-        if (j < sb) X[(int64_t)(o + i) * ldx + o + j] = Xs[i][j];
+    for (int e = threadIdx.x; e < sb * sb; e += BT) {
+        const int i = e / sb, c = e % sb;
+        X[(int64_t)(o + i) * ldx + o + c] = Xs[i][c];
+    }
 }
 
 }  // namespace
@@ -110,7 +159,10 @@ pluq_status tri_inv_lower_unit(const uint32_t *L, int64_t ldl, Blk X, int64_t r,
     if (r <= 0) return PLUQ_OK;
     PLUQ_TRY(launch_zero(X, r, r, st));
     prof::start(prof::TRI, st);
-    inv_lower_unit_base<<<(unsigned)ceil_div(r, TB), TB, 0, st>>>(L, ldl, X.ptr, X.ld, (int)r, F);
+    if (F.p <= 65536u)
+        inv_lower_unit_base<true><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(L, ldl, X.ptr, X.ld, (int)r, F);
+    else
+        inv_lower_unit_base<false><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(L, ldl, X.ptr, X.ld, (int)r, F);
     PLUQ_TRY(last_launch());
     prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;
@@ -148,7 +200,10 @@ pluq_status tri_inv_upper(const uint32_t *U, int64_t ldu, Blk X, int64_t r, Fiel
     if (r <= 0) return PLUQ_OK;
     PLUQ_TRY(launch_zero(X, r, r, st));
     prof::start(prof::TRI, st);
-    inv_upper_base<<<(unsigned)ceil_div(r, TB), TB, 0, st>>>(U, ldu, X.ptr, X.ld, (int)r, F);
+    if (F.p <= 65536u)
+        inv_upper_base<true><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(U, ldu, X.ptr, X.ld, (int)r, F);
+    else
+        inv_upper_base<false><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(U, ldu, X.ptr, X.ld, (int)r, F);
     PLUQ_TRY(last_launch());
     prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;

@@ -342,3 +342,26 @@ def test_trsm_solves():
             B2 = g.integers(0, p, (N, r)).astype(np.uint32)
             X2 = oracle.trsm_right_upper(U, B2, p)
             assert np.array_equal(brute.matmul_mod(X2, U, p), B2.astype(np.int64))
+
+
+def test_descent_free_profiles_are_met_in_row_order():
+    """When the ones of R have increasing columns in row order, Algorithm 1's
+    recursion meets them in row order (checked against the literal reading)."""
+    g = np.random.Generator(np.random.PCG64(21))
+    for _ in range(40):
+        m, n = int(g.integers(2, 40)), int(g.integers(2, 40))
+        r = int(g.integers(0, min(m, n) + 1))
+        rows = np.sort(g.choice(m, r, replace=False))
+        cols = np.sort(g.choice(n, r, replace=False))        # increasing with the rows
+        col = np.full(m, -1, dtype=np.int32)
+        col[rows] = cols
+        pr, pc = oracle.canonical_order(m, n, col)
+        assert np.array_equal(pr, rows) and np.array_equal(pc, cols)
+        # and the literal Algorithm 1 agrees on a matrix with that profile
+        Lc = np.tril(g.integers(0, 7, (m, m)), -1) + np.eye(m, dtype=np.int64)
+        Uc = np.triu(g.integers(0, 7, (n, n)), 1) + np.eye(n, dtype=np.int64)
+        Rm = np.zeros((m, n), dtype=np.int64)
+        Rm[rows, cols] = 1
+        A = brute.matmul_mod(brute.matmul_mod(Lc, Rm, 7), Uc, 7).astype(np.uint32)
+        _, pp, pq, rr = oracle.pluq_alg1(A, 7)
+        assert rr == r and np.array_equal(pp[:r], rows) and np.array_equal(pq[:r], cols)
