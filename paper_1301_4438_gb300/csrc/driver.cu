@@ -26,6 +26,8 @@ pluq_status launch_rank_sort(const int32_t *key, const int32_t *val, int64_t r, 
                              int32_t *out_val, cudaStream_t st);
 pluq_status launch_check_range(const uint32_t *A, int64_t lda, int64_t m, int64_t n, uint32_t p,
                                int32_t *flag, cudaStream_t st);
+pluq_status launch_any_nonzero(const uint32_t *A, int64_t lda, int64_t m, int64_t n, int32_t *words,
+                               volatile int32_t *host, int32_t seq, cudaStream_t st);
 
 namespace {
 // byte ranges [lo, hi) spanned by a batch of strided blocks
@@ -121,6 +123,7 @@ struct Ctx {
     HostWords *hw;
     int64_t leaf = 64;    // blocks with both sides <= leaf go to the leaf kernel
     int64_t leaves = 0;
+    int64_t zero_checks = 0;
 };
 
 // Leaf size of the recursion: PLUQ_LEAF (16..128) if set, else 64.  Smaller
@@ -195,6 +198,16 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
         out.pid = c.hw->h[2] != 0;
         out.qid = c.hw->h[3] != 0;
         return PLUQ_OK;
+    }
+    // A block's rank is the number of ones of R inside it, so deep in the
+    // recursion of a rank-deficient matrix most blocks are exactly zero: one
+    // pass over the block prunes the whole subtree (r = 0, P = Q = I).
+    {
+        const int32_t seq = ++c.hw->seq;
+        PLUQ_TRY(launch_any_nonzero(A, lda, m, n, c.d_rank + 8, c.hw->d, seq, c.st));
+        PLUQ_TRY(wait_words(c.hw, seq, c.st));
+        ++c.zero_checks;
+        if (c.hw->h[1] == 0) return PLUQ_OK;
     }
     const int64_t k = m / 2, h = n / 2;
     const size_t vmark = c.vtop;
@@ -382,7 +395,7 @@ pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_
 
     // every entry must already be reduced: checked before anything is written
     int32_t flag = 0;
-    PLUQ_CUDA_TRY(cudaMemsetAsync(c.d_rank, 0, sizeof(int32_t), st));
+    PLUQ_CUDA_TRY(cudaMemsetAsync(c.d_rank, 0, 64, st));
     PLUQ_TRY(launch_check_range(d_A, lda, m, n, p, c.d_rank, st));
     PLUQ_CUDA_TRY(cudaMemcpyAsync(&flag, c.d_rank, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PLUQ_CUDA_TRY(cudaStreamSynchronize(st));

@@ -135,6 +135,35 @@ __global__ void check_range_kernel(const uint32_t *__restrict__ A, int64_t lda, 
         }
 }
 
+// Any nonzero in the m x n block?  Blocks OR their finding into words[0] and
+// count themselves in words[1]; the last block publishes the answer to the
+// mapped host words (flag, then sequence number) and clears both counters.
+__global__ void any_nonzero_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t m,
+                                   int64_t n, int32_t *words, volatile int32_t *host, int32_t seq)
+{
+    const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
+    bool nz = false;
+    for (int64_t i = blockIdx.y; i < m && !nz; i += gridDim.y)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int64_t j = c0 + (int64_t)s * GT;
+            if (j < n && A[i * lda + j] != 0) nz = true;
+        }
+    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&words[0], 1);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned total = gridDim.x * gridDim.y;
+        if ((unsigned)atomicAdd(&words[1], 1) == total - 1) {
+            const int32_t f = atomicOr(&words[0], 0);
+            words[0] = 0;
+            words[1] = 0;
+            host[1] = f;
+            __threadfence_system();
+            host[0] = seq;
+        }
+    }
+}
+
 dim3 grid2d(int64_t rows, int64_t cols)
 {
     int64_t gy = rows < 65535 ? rows : 65535;
@@ -205,4 +234,15 @@ pluq_status launch_check_range(const uint32_t *A, int64_t lda, int64_t m, int64_
     return last_launch();
 }
 
+}  // namespace pluq
+
+namespace pluq {
+pluq_status launch_any_nonzero(const uint32_t *A, int64_t lda, int64_t m, int64_t n, int32_t *words,
+                               volatile int32_t *host, int32_t seq, cudaStream_t st)
+{
+    int64_t gy = m < 1024 ? m : 1024;
+    dim3 grid((unsigned)ceil_div(n, GC), (unsigned)(gy > 0 ? gy : 1));
+    any_nonzero_kernel<<<grid, GT, 0, st>>>(A, lda, m, n, words, host, seq);
+    return last_launch();
+}
 }  // namespace pluq

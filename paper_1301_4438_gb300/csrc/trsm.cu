@@ -239,7 +239,18 @@ size_t trsm_workspace(int64_t r, int64_t other, uint32_t p, int kind)
 {
     size_t w = 2 * (size_t)r * r * sizeof(uint32_t) + 4096;        // X and T
     w += (size_t)r * other * sizeof(uint32_t) + 256;               // result staging
-    if (kind != PLUQ_MM_SIMT) w += mm_tc_workspace(other, r, r, p, 1) + mm_tc_workspace(r, r, r, p, 64);
+    if (kind != PLUQ_MM_SIMT) {
+        // limb planes: the solve's product, or the largest batched merge level
+        size_t tc = mm_tc_workspace(other, r, r, p, 1);
+        const size_t left = mm_tc_workspace(r, other, r, p, 1);
+        if (left > tc) tc = left;
+        for (int64_t s = TB; s < r; s *= 2) {
+            const int64_t full = r / (2 * s);
+            const size_t lv = mm_tc_workspace(s, s, s, p, full > 0 ? full : 1);
+            if (lv > tc) tc = lv;
+        }
+        w += tc;
+    }
     return w;
 }
 
