@@ -87,6 +87,27 @@ pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_
                        void *d_work, size_t ws_bytes, int mm_kind, void *stream);
 
 /*
+ * Many independent decompositions of uneven sizes (the families of matrices
+ * Groebner-basis elimination produces), each with the contract of
+ * pluq_mod_p.  Host arrays of length `count` give, per matrix, its device
+ * pointer h_dA[i] (m[i] x n[i], stride lda[i]), its output vectors
+ * h_dperm_p[i] / h_dperm_q[i] (device) and receive h_rank[i].  `workers` host
+ * threads, each with its own non-blocking stream (created and destroyed inside
+ * the call, ordered after the work already queued on `stream`) and its own
+ * slice of d_work, take the matrices largest first; the kernels of different
+ * matrices overlap on the GPU.  Returns after every decomposition is done;
+ * the first failing status is returned (later matrices are then skipped).
+ * Workspace: pluq_batched_workspace_size (workers x the largest single need).
+ */
+pluq_status pluq_batched_workspace_size(const int64_t *h_m, const int64_t *h_n, int64_t count,
+                                        uint32_t p, int workers, size_t *h_bytes);
+pluq_status pluq_mod_p_batched(uint32_t *const *h_dA, const int64_t *h_m, const int64_t *h_n,
+                               const int64_t *h_lda, int64_t count, uint32_t p,
+                               int32_t *const *h_dperm_p, int32_t *const *h_dperm_q,
+                               int64_t *h_rank, void *d_work, size_t ws_bytes, int mm_kind,
+                               int workers, void *stream);
+
+/*
  * Row rank profile of A (Corollary of Lemma 2, Sec. 4): the sorted first r
  * entries of perm_p.  d_out receives r int32.  Asynchronous on `stream`.
  */

@@ -6,8 +6,12 @@
 // continues; everything else is queued asynchronously.  Blocks are addressed
 // in place inside the caller's matrix (pointer + row stride); permutations of
 // a block go through a scratch copy.
+#include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <vector>
 #include <stdlib.h>
 #include <string.h>
 
@@ -71,29 +75,48 @@ bool is_prime_u32(uint32_t p)
     return true;
 }
 
-// Mapped pinned host words (one block per host thread): the leaf kernel
-// writes its rank and identity flags there and then a sequence number, and
-// the host polls the sequence number instead of copying and synchronising.
+// Mapped pinned host words: a kernel writes its result words and then a
+// sequence number there, and the host polls the sequence number instead of
+// copying and synchronising.  Slots come from a process-wide pool so that
+// concurrent callers (and the batch workers) each own one while they run.
 struct HostWords {
-    volatile int32_t *h = nullptr;   // host view
+    volatile int32_t *h = nullptr;   // host view (64 words)
     int32_t *d = nullptr;            // device view
     int32_t seq = 0;
 };
-HostWords *host_words()
+std::mutex g_words_mu;
+std::vector<HostWords *> g_words_free;
+
+HostWords *acquire_words()
 {
-    thread_local HostWords hw;
-    if (!hw.h) {
+    std::lock_guard<std::mutex> lk(g_words_mu);
+    if (g_words_free.empty()) {
+        constexpr int SLOTS = 16, BYTES = 256;
         int32_t *h = nullptr;
-        if (cudaHostAlloc((void **)&h, 256, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        if (cudaHostAlloc((void **)&h, SLOTS * BYTES, cudaHostAllocMapped | cudaHostAllocPortable) !=
             cudaSuccess)
             return nullptr;
         int32_t *d = nullptr;
         if (cudaHostGetDevicePointer((void **)&d, h, 0) != cudaSuccess) return nullptr;
-        for (int i = 0; i < 64; ++i) h[i] = 0;
-        hw.h = h;
-        hw.d = d;
+        for (int i = 0; i < SLOTS * BYTES / 4; ++i) h[i] = 0;
+        for (int sl = 0; sl < SLOTS; ++sl) {
+            HostWords *w = new (std::nothrow) HostWords;
+            if (!w) return nullptr;
+            w->h = h + sl * (BYTES / 4);
+            w->d = d + sl * (BYTES / 4);
+            g_words_free.push_back(w);
+        }
     }
-    return &hw;
+    HostWords *w = g_words_free.back();
+    g_words_free.pop_back();
+    return w;
+}
+
+void release_words(HostWords *w)
+{
+    if (!w) return;
+    std::lock_guard<std::mutex> lk(g_words_mu);
+    g_words_free.push_back(w);
 }
 
 // wait for the leaf kernel to publish sequence number `seq` (bounded)
@@ -351,27 +374,23 @@ pluq_status pluq_workspace_size(int64_t m, int64_t n, uint32_t p, size_t *h_byte
     return PLUQ_OK;
 }
 
-pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
-                       int32_t *d_perm_p, int32_t *d_perm_q, int64_t *h_rank, void *d_work,
-                       size_t ws_bytes, int mm_kind, void *stream)
+}  // extern "C"
+
+namespace pluq {
+namespace {
+
+// One decomposition on `st` with scratch at `w` (validated by the caller).
+pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                    int32_t *d_perm_p, int32_t *d_perm_q, int64_t *h_rank, char *w, int kind,
+                    cudaStream_t st, HostWords *hw)
 {
-    if (m < 0 || n < 0 || !h_rank) return PLUQ_EINVAL;
-    if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return PLUQ_EINVAL;
-    if (mm_kind < PLUQ_MM_AUTO || mm_kind > PLUQ_MM_TENSOR) return PLUQ_EINVAL;
-    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
-    if ((m > 0 && !d_perm_p) || (n > 0 && !d_perm_q)) return PLUQ_EINVAL;
-    if (m > 0 && n > 0 && (!d_A || lda < n)) return PLUQ_EINVAL;
-    const int kind = resolve_kind(mm_kind);
     Layout L = layout(m, n, p, kind);
-    if (!d_work || ws_bytes < L.total) return PLUQ_ENOMEM;
-    cudaStream_t st = (cudaStream_t)stream;
     *h_rank = 0;
     if (m == 0 || n == 0) {
         PLUQ_TRY(launch_iota(d_perm_p, m, st));
         PLUQ_TRY(launch_iota(d_perm_q, n, st));
         return PLUQ_OK;
     }
-    char *w = (char *)d_work;
     Ctx c;
     c.F = make_field(p);
     c.kind = kind;
@@ -389,8 +408,7 @@ pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_
     c.ar.base = w;
     c.ar.size = L.arena;
     c.ar.off = 0;
-    c.hw = host_words();
-    if (!c.hw) return PLUQ_ECUDA;
+    c.hw = hw;
     c.leaf = leaf_size();
 
     // every entry must already be reduced: checked before anything is written
@@ -409,6 +427,130 @@ pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_
     if (tc_error_flag()) return PLUQ_ETIMEOUT;
     *h_rank = res.r;
     return PLUQ_OK;
+}
+
+pluq_status check_args(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, int32_t *d_perm_p,
+                       int32_t *d_perm_q)
+{
+    if (m < 0 || n < 0) return PLUQ_EINVAL;
+    if (m > (1ll << 31) - 1 || n > (1ll << 31) - 1) return PLUQ_EINVAL;
+    if ((m > 0 && !d_perm_p) || (n > 0 && !d_perm_q)) return PLUQ_EINVAL;
+    if (m > 0 && n > 0 && (!d_A || lda < n)) return PLUQ_EINVAL;
+    return PLUQ_OK;
+}
+
+}  // namespace
+}  // namespace pluq
+
+extern "C" {
+
+pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+                       int32_t *d_perm_p, int32_t *d_perm_q, int64_t *h_rank, void *d_work,
+                       size_t ws_bytes, int mm_kind, void *stream)
+{
+    if (!h_rank) return PLUQ_EINVAL;
+    PLUQ_TRY(check_args(d_A, m, n, lda, d_perm_p, d_perm_q));
+    if (mm_kind < PLUQ_MM_AUTO || mm_kind > PLUQ_MM_TENSOR) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    const int kind = resolve_kind(mm_kind);
+    if (!d_work || ws_bytes < layout(m, n, p, kind).total) return PLUQ_ENOMEM;
+    HostWords *hw = acquire_words();
+    if (!hw) return PLUQ_ECUDA;
+    pluq_status s = run_one(d_A, m, n, lda, p, d_perm_p, d_perm_q, h_rank, (char *)d_work, kind,
+                            (cudaStream_t)stream, hw);
+    release_words(hw);
+    return s;
+}
+
+pluq_status pluq_batched_workspace_size(const int64_t *h_m, const int64_t *h_n, int64_t count,
+                                        uint32_t p, int workers, size_t *h_bytes)
+{
+    if (count < 0 || workers < 1 || !h_bytes || (count > 0 && (!h_m || !h_n))) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    size_t mx = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (h_m[i] < 0 || h_n[i] < 0) return PLUQ_EINVAL;
+        const size_t w = layout(h_m[i], h_n[i], p, PLUQ_MM_TENSOR).total;
+        if (w > mx) mx = w;
+    }
+    const int64_t used = count < workers ? (count > 0 ? count : 1) : workers;
+    *h_bytes = align_up(mx, 4096) * (size_t)used;
+    return PLUQ_OK;
+}
+
+pluq_status pluq_mod_p_batched(uint32_t *const *h_dA, const int64_t *h_m, const int64_t *h_n,
+                               const int64_t *h_lda, int64_t count, uint32_t p,
+                               int32_t *const *h_dperm_p, int32_t *const *h_dperm_q,
+                               int64_t *h_rank, void *d_work, size_t ws_bytes, int mm_kind,
+                               int workers, void *stream)
+{
+    if (count < 0 || workers < 1) return PLUQ_EINVAL;
+    if (count == 0) return PLUQ_OK;
+    if (!h_dA || !h_m || !h_n || !h_lda || !h_dperm_p || !h_dperm_q || !h_rank) return PLUQ_EINVAL;
+    if (mm_kind < PLUQ_MM_AUTO || mm_kind > PLUQ_MM_TENSOR) return PLUQ_EINVAL;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
+    for (int64_t i = 0; i < count; ++i)
+        PLUQ_TRY(check_args(h_dA[i], h_m[i], h_n[i], h_lda[i], h_dperm_p[i], h_dperm_q[i]));
+    size_t need = 0;
+    PLUQ_TRY(pluq_batched_workspace_size(h_m, h_n, count, p, workers, &need));
+    if (!d_work || ws_bytes < need) return PLUQ_ENOMEM;
+    const int kind = resolve_kind(mm_kind);
+    const int T = (int)(count < workers ? count : workers);
+    const size_t slice = need / (size_t)T;
+
+    // largest matrices first, so the tail of the batch is made of small ones
+    std::vector<int64_t> order(count);
+    for (int64_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return h_m[a] * h_n[a] > h_m[b] * h_n[b];
+    });
+
+    int dev = 0;
+    PLUQ_CUDA_TRY(cudaGetDevice(&dev));
+    cudaEvent_t start;
+    PLUQ_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    if (cudaEventRecord(start, (cudaStream_t)stream) != cudaSuccess) {
+        cudaEventDestroy(start);
+        return PLUQ_ECUDA;
+    }
+    std::atomic<int64_t> next{0};
+    std::atomic<int> first_err{PLUQ_OK};
+    auto worker = [&](int t) {
+        if (cudaSetDevice(dev) != cudaSuccess) { first_err.store(PLUQ_ECUDA); return; }
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            first_err.store(PLUQ_ECUDA);
+            return;
+        }
+        HostWords *hw = acquire_words();
+        if (!hw || cudaStreamWaitEvent(st, start, 0) != cudaSuccess) {
+            first_err.store(PLUQ_ECUDA);
+        } else {
+            char *w = (char *)d_work + (size_t)t * slice;
+            for (;;) {
+                if (first_err.load() != PLUQ_OK) break;
+                const int64_t q = next.fetch_add(1);
+                if (q >= count) break;
+                const int64_t i = order[q];
+                pluq_status s = run_one(h_dA[i], h_m[i], h_n[i], h_lda[i], p, h_dperm_p[i],
+                                        h_dperm_q[i], &h_rank[i], w, kind, st, hw);
+                if (s != PLUQ_OK) {
+                    int expect = PLUQ_OK;
+                    first_err.compare_exchange_strong(expect, (int)s);
+                    break;
+                }
+            }
+        }
+        release_words(hw);
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(T);
+    for (int t = 0; t < T; ++t) pool.emplace_back(worker, t);
+    for (auto &th : pool) th.join();
+    cudaEventDestroy(start);
+    return (pluq_status)first_err.load();
 }
 
 pluq_status row_rank_profile(const int32_t *d_perm_p, int64_t m, int64_t r, int32_t *d_out,

@@ -590,14 +590,10 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     pluq_status ls = PLUQ_OK;
 #define PLUQ_LEAF_CASE(SP, C, R)                                                                  \
     if (small == SP && cpl == C && rpw == R) {                                                   \
-        static bool attr = false;                                                                \
-        if (!attr) {                                                                             \
-            if (cudaFuncSetAttribute(leaf_kernel<SP, C, R>,                                      \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=  \
-                cudaSuccess)                                                                     \
-                return PLUQ_ECUDA;                                                               \
-            attr = true;                                                                         \
-        }                                                                                        \
+        static const bool attr = cudaFuncSetAttribute(leaf_kernel<SP, C, R>,                     \
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                      (int)smem) == cudaSuccess;                 \
+        if (!attr) return PLUQ_ECUDA;                                                            \
         leaf_kernel<SP, C, R><<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q,    \
                                                    info, info_len, host_info, seq);              \
     }

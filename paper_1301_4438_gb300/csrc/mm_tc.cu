@@ -443,15 +443,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 EncodeTiledFn encode_fn()
 {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // thread-safe one-time lookup (function-local static initialisation)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                              &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
+            return (EncodeTiledFn)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -497,13 +498,10 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
     if (!make_map(&ma, pa, batch * L * Mp, Kp, BM)) return PLUQ_ECUDA;
     if (!make_map(&mb, pb, batch * L * Np, Kp, G::BN)) return PLUQ_ECUDA;
 
-    static bool attr = false;
-    if (!attr) {
-        PLUQ_CUDA_TRY(cudaFuncSetAttribute(mm_tc_kernel<L>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)G::SMEM));
-        attr = true;
-    }
+    static const bool attr = cudaFuncSetAttribute(mm_tc_kernel<L>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)G::SMEM) == cudaSuccess;
+    if (!attr) return PLUQ_ECUDA;
     TcArgs a;
     a.C = C.ptr;
     a.ldc = C.ld;

@@ -55,6 +55,10 @@ _SIGS = {
     "pluq_leaf": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_u32, _vp, _vp, _vp, _vp]),
     "pluq_modmm_tensor_noalloc": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _c_i64,
                                                  _c_i64, _c_i64, _c_u32, ctypes.c_int, _vp]),
+    "pluq_batched_workspace_size": (ctypes.c_int, [_i64p, _i64p, _c_i64, _c_u32, ctypes.c_int, _szp]),
+    "pluq_mod_p_batched": (ctypes.c_int, [ctypes.POINTER(_vp), _i64p, _i64p, _i64p, _c_i64, _c_u32,
+                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64p, _vp,
+                                          ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _vp]),
     "pluq_launch_count": (ctypes.c_longlong, []),
     "pluq_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pluq_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -302,3 +306,44 @@ def pluq_profile_read(kernel_class):
     _check(load().pluq_profile_read(cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(w)),
            "pluq_profile_read")
     return int(n.value), float(ms.value), float(w.value)
+
+
+def pluq_batched_workspace_size(shapes, p: int, workers: int = 8) -> int:
+    cnt = len(shapes)
+    ms = (ctypes.c_int64 * max(cnt, 1))(*[int(a) for a, _ in shapes])
+    ns = (ctypes.c_int64 * max(cnt, 1))(*[int(b) for _, b in shapes])
+    out = ctypes.c_size_t(0)
+    _check(load().pluq_batched_workspace_size(ms, ns, cnt, p, workers, ctypes.byref(out)),
+           "pluq_batched_workspace_size")
+    return int(out.value)
+
+
+def pluq_mod_p_batched(mats, p: int, mm: str = "auto", workers: int = 8, workspace=None,
+                       stream=None):
+    """In-place PLUQ of every matrix in `mats` (int32 CUDA tensors, rows
+    contiguous).  Returns (list of perm_p, list of perm_q, list of ranks)."""
+    _need_cuda(*mats)
+    cnt = len(mats)
+    if cnt == 0:
+        return [], [], []
+    dev = mats[0].device
+    shapes = [tuple(A.shape) for A in mats]
+    pps = [torch.empty(max(m, 1), dtype=torch.int32, device=dev) for m, _ in shapes]
+    pqs = [torch.empty(max(n, 1), dtype=torch.int32, device=dev) for _, n in shapes]
+    ws = pluq_batched_workspace_size(shapes, p, workers)
+    if workspace is None or workspace.numel() < ws:
+        workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+    VP = _vp * cnt
+    I64 = ctypes.c_int64 * cnt
+    a_ptrs = VP(*[A.data_ptr() if A.numel() else 0 for A in mats])
+    p_ptrs = VP(*[t.data_ptr() for t in pps])
+    q_ptrs = VP(*[t.data_ptr() for t in pqs])
+    ms = I64(*[m for m, _ in shapes])
+    ns = I64(*[n for _, n in shapes])
+    lds = I64(*[(A.stride(0) if A.shape[0] else max(A.shape[1], 1)) for A in mats])
+    ranks = I64()
+    _check(load().pluq_mod_p_batched(a_ptrs, ms, ns, lds, cnt, p, p_ptrs, q_ptrs, ranks,
+                                     _ptr(workspace), workspace.numel(), _KIND[mm], workers,
+                                     _stream(stream)), "pluq_mod_p_batched")
+    return ([pps[i][:shapes[i][0]] for i in range(cnt)], [pqs[i][:shapes[i][1]] for i in range(cnt)],
+            [int(ranks[i]) for i in range(cnt)])

@@ -211,3 +211,53 @@ def batch_2000(count: int = 2000, lo: int = 64, hi: int = 2048, p: int = 65521,
     rs = [min(a, b) // 2 for a, b in zip(ms, ns)]
     seeds = [seed * 7919 + i for i in range(count)]
     return Batch(p, ms, ns, rs, seeds)
+
+
+def planted_device(m: int, n: int, r: int, p: int, seed: int, device: str):
+    """Planted-profile matrix drawn with torch's generator on `device` (for
+    batches too large to draw on the host).  Returns (A int32 tensor,
+    rows, cols) with R[rows[t], cols[t]] = 1 as numpy int64 arrays."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    rows = torch.sort(torch.randperm(m, generator=g, device=device)[:r]).values
+    cols = torch.sort(torch.randperm(n, generator=g, device=device)[:r]).values
+    cols = cols[torch.randperm(r, generator=g, device=device)]
+    Lc = torch.randint(0, p, (m, r), generator=g, device=device, dtype=torch.int64)
+    Ur = torch.randint(0, p, (r, n), generator=g, device=device, dtype=torch.int64)
+    ii = torch.arange(m, device=device)[:, None]
+    jj = torch.arange(n, device=device)[None, :]
+    Lc = torch.where(ii < rows[None, :], torch.zeros_like(Lc), Lc)
+    Lc[rows, torch.arange(r, device=device)] = 1
+    Ur = torch.where(jj < cols[:, None], torch.zeros_like(Ur), Ur)
+    Ur[torch.arange(r, device=device), cols] = 1
+    if r == 0:
+        A = torch.zeros((m, n), dtype=torch.int32, device=device)
+    else:
+        A = _product_torch_t(Lc, Ur, p).to(torch.int32)
+    return A, rows.cpu().numpy().astype(np.int64), cols.cpu().numpy().astype(np.int64)
+
+
+def _product_torch_t(A, B, p: int):
+    """Exact (A B) mod p for int64 CUDA tensors with entries in [0, p)."""
+    import torch
+    m, r = A.shape
+    n = B.shape[1]
+    nl = max(1, (int(p - 1).bit_length() + 7) // 8)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        acc = [torch.zeros((m, n), dtype=torch.float64, device=A.device) for _ in range(2 * nl - 1)]
+        for s in range(0, r, 256):
+            e = min(r, s + 256)
+            al = [((A[:, s:e] >> (8 * i)) & 255).to(torch.float32) for i in range(nl)]
+            bl = [((B[s:e] >> (8 * j)) & 255).to(torch.float32) for j in range(nl)]
+            for i in range(nl):
+                for j in range(nl):
+                    acc[i + j] += (al[i] @ bl[j]).to(torch.float64)
+        out = torch.zeros((m, n), dtype=torch.int64, device=A.device)
+        for s_, a in enumerate(acc):
+            out = (out + (a.to(torch.int64) % p) * pow(256, s_, p)) % p
+        return out
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
