@@ -12,7 +12,8 @@
 //   - the solve is X B (or B X).
 // The inverse costs r^3/3 field operations, small next to the r^2 N of the
 // solve for the shapes Algorithm 1 produces, and the launches per TRSM drop
-// from O(r/32) to O(log(r/32)).
+// from O(r/32) to O(log(r/32)).  Triangles of at most 64 rows are solved
+// directly by substitution instead (one launch).
 #include "common.cuh"
 
 namespace pluq {
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(BT) inv_lower_unit_base(const uint32_t *__rest
     const int o = blockIdx.x * TB;
     const int sb = min(TB, r - o);
     const int j = threadIdx.x % TB, g = threadIdx.x / TB;
+#pragma unroll 16
     for (int e = threadIdx.x; e < TB * TB; e += BT) {
         const int i = e / TB, c = e % TB;
         Ls[i][c] = (i < sb && c < sb) ? L[(int64_t)(o + i) * ldl + o + c] : 0u;
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(BT) inv_upper_base(const uint32_t *__restrict_
     const int o = blockIdx.x * TB;
     const int sb = min(TB, r - o);
     const int j = threadIdx.x % TB, g = threadIdx.x / TB;
+#pragma unroll 16
     for (int e = threadIdx.x; e < TB * TB; e += BT) {
         const int i = e / TB, c = e % TB;
         Us[i][c] = (i < sb && c < sb) ? U[(int64_t)(o + i) * ldu + o + c] : 0u;
@@ -148,6 +151,93 @@ __global__ void __launch_bounds__(BT) inv_upper_base(const uint32_t *__restrict_
     for (int e = threadIdx.x; e < sb * sb; e += BT) {
         const int i = e / sb, c = e % sb;
         X[(int64_t)(o + i) * ldx + o + c] = Xs[i][c];
+    }
+}
+
+// Direct solves for narrow triangles (r <= 64): one launch, the triangle and
+// the right-hand sides in shared memory, one thread per column (left) or row
+// (right) of B.  Each dot product is split over four independent running
+// sums; the code stays compact (a rolled loop), which matters more here than
+// unrolling.
+constexpr int DR = 64, DT = 64;
+
+template <bool SMALLP>
+__device__ __forceinline__ uint32_t dot4(const uint32_t *a, int astride, const uint32_t *b,
+                                         int bstride, int len, const Field &F, uint32_t w16)
+{
+    Acc<SMALLP> s0, s1, s2, s3;
+    int l = 0;
+    for (; l + 4 <= len; l += 4) {
+        s0.add(a[(l + 0) * astride], b[(l + 0) * bstride]);
+        s1.add(a[(l + 1) * astride], b[(l + 1) * bstride]);
+        s2.add(a[(l + 2) * astride], b[(l + 2) * bstride]);
+        s3.add(a[(l + 3) * astride], b[(l + 3) * bstride]);
+    }
+    for (; l < len; ++l) s0.add(a[l * astride], b[l * bstride]);
+    s0.lo += s1.lo + s2.lo + s3.lo;      // at most 64 products in all: no overflow
+    s0.hi += s1.hi + s2.hi + s3.hi;
+    return s0.value(F, w16);
+}
+
+// B (r x N) <- L^{-1} B, L unit lower; a block owns DT consecutive columns.
+template <bool SMALLP>
+__global__ void __launch_bounds__(DT) trsm_left_direct(const uint32_t *__restrict__ L, int64_t ldl,
+                                                        uint32_t *__restrict__ B, int64_t ldb,
+                                                        int r, int64_t N, Field F)
+{
+    __shared__ uint32_t Ls[DR][DR + 1];
+    __shared__ uint32_t X[DR][DT];
+    const int64_t j0 = (int64_t)blockIdx.x * DT;
+    const int tx = threadIdx.x;
+#pragma unroll 16
+    for (int e = tx; e < r * r; e += DT) {
+        const int i = e / r, c = e % r;
+        Ls[i][c] = L[(int64_t)i * ldl + c];
+    }
+    const bool ok = j0 + tx < N;
+#pragma unroll 16
+    for (int i = 0; i < r; ++i) X[i][tx] = ok ? B[(int64_t)i * ldb + j0 + tx] : 0u;
+    __syncthreads();
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    for (int i = 1; i < r; ++i)
+        X[i][tx] = sub_mod(X[i][tx], dot4<SMALLP>(&Ls[i][0], 1, &X[0][tx], DT, i, F, w16), F.p);
+    if (ok)
+        for (int i = 0; i < r; ++i) B[(int64_t)i * ldb + j0 + tx] = X[i][tx];
+}
+
+// B (M x r) <- B U^{-1}, U upper with nonzero diagonal; a block owns DT rows.
+template <bool SMALLP>
+__global__ void __launch_bounds__(DT) trsm_right_direct(const uint32_t *__restrict__ U, int64_t ldu,
+                                                         uint32_t *__restrict__ B, int64_t ldb,
+                                                         int64_t M, int r, Field F)
+{
+    __shared__ uint32_t Us[DR][DR + 1];
+    __shared__ uint32_t X[DT][DR + 1];
+    __shared__ uint32_t dinv[DR];
+    const int64_t i0 = (int64_t)blockIdx.x * DT;
+    const int tx = threadIdx.x;
+#pragma unroll 16
+    for (int e = tx; e < r * r; e += DT) {
+        const int i = e / r, c = e % r;
+        Us[i][c] = U[(int64_t)i * ldu + c];
+    }
+#pragma unroll 16
+    for (int e = tx; e < DT * r; e += DT) {
+        const int i = e / r, c = e % r;
+        X[i][c] = i0 + i < M ? B[(i0 + i) * ldb + c] : 0u;
+    }
+    __syncthreads();
+    if (tx < r) dinv[tx] = inv_mod(Us[tx][tx], F.p);
+    __syncthreads();
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    for (int j = 0; j < r; ++j) {
+        const uint32_t s = dot4<SMALLP>(&X[tx][0], 1, &Us[0][j], DR + 1, j, F, w16);
+        X[tx][j] = mul_mod(sub_mod(X[tx][j], s, F.p), dinv[j], F);
+    }
+    __syncthreads();
+    for (int e = tx; e < DT * r; e += DT) {
+        const int i = e / r, c = e % r;
+        if (i0 + i < M) B[(i0 + i) * ldb + c] = X[i][c];
     }
 }
 
@@ -258,6 +348,16 @@ pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t 
                                  Field F, int kind, Arena &ar, cudaStream_t st)
 {
     if (r <= 0 || N <= 0) return PLUQ_OK;
+    if (r <= DR) {
+        prof::start(prof::TRI, st);
+        if (F.p <= 65536u)
+            trsm_left_direct<true><<<(unsigned)ceil_div(N, DT), DT, 0, st>>>(L, ldl, B.ptr, B.ld, (int)r, N, F);
+        else
+            trsm_left_direct<false><<<(unsigned)ceil_div(N, DT), DT, 0, st>>>(L, ldl, B.ptr, B.ld, (int)r, N, F);
+        pluq_status s = last_launch();
+        prof::stop(prof::TRI, st, (double)r * r * N / 2.0);
+        return s;
+    }
     size_t mark = ar.off;
     uint32_t *X = (uint32_t *)ar.take((size_t)r * r * sizeof(uint32_t));
     if (!X) return PLUQ_ENOMEM;
@@ -279,6 +379,16 @@ pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, i
                              Field F, int kind, Arena &ar, cudaStream_t st)
 {
     if (r <= 0 || M <= 0) return PLUQ_OK;
+    if (r <= DR) {
+        prof::start(prof::TRI, st);
+        if (F.p <= 65536u)
+            trsm_right_direct<true><<<(unsigned)ceil_div(M, DT), DT, 0, st>>>(U, ldu, B.ptr, B.ld, M, (int)r, F);
+        else
+            trsm_right_direct<false><<<(unsigned)ceil_div(M, DT), DT, 0, st>>>(U, ldu, B.ptr, B.ld, M, (int)r, F);
+        pluq_status s = last_launch();
+        prof::stop(prof::TRI, st, (double)r * r * M / 2.0);
+        return s;
+    }
     size_t mark = ar.off;
     uint32_t *X = (uint32_t *)ar.take((size_t)r * r * sizeof(uint32_t));
     if (!X) return PLUQ_ENOMEM;
