@@ -47,7 +47,43 @@ def parse():
     ap.add_argument("--workload", default="dense_4096")
     ap.add_argument("--mm", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["pluq", "gemm", "leaf"], default=None,
+                    help="untimed: one warm-up and one decomposition of the workload (pluq), one "
+                         "modular product of --shape M,N,K (gemm), or one base-case call on a "
+                         "uniform --shape M,N block (leaf), for external profilers")
+    ap.add_argument("--shape", default="8192,8192,2048", help="sizes for --profile gemm / leaf")
+    ap.add_argument("--p", type=int, default=65521, help="modulus for --profile gemm")
     return ap.parse_args()
+
+
+def run_profile_target(args):
+    import torch
+    from paper_1301_4438_gb300 import pluq, workloads as W
+    if args.profile == "leaf":
+        m, n = (int(x) for x in args.shape.split(",")[:2])
+        A0 = torch.from_numpy(W.uniform(m, n, args.p, W.BASE_SEED + 5).astype(np.int32)).cuda()
+        for _ in range(2):
+            pluq.pluq_leaf(A0.clone(), args.p)
+    elif args.profile == "gemm":
+        M, N, K = (int(x) for x in args.shape.split(","))
+        p = args.p
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1)
+        A = torch.randint(0, p, (M, K), generator=g, device="cuda", dtype=torch.int64).to(torch.int32)
+        B = torch.randint(0, p, (K, N), generator=g, device="cuda", dtype=torch.int64).to(torch.int32)
+        C = torch.randint(0, p, (M, N), generator=g, device="cuda", dtype=torch.int64).to(torch.int32)
+        for _ in range(2):
+            pluq.pluq_modmm(C, A, B, p, mm=args.mm)
+    else:
+        cfg = W.CONFIGS[args.workload]
+        A0, _ = W.make(cfg, device="cuda")
+        A0 = A0.to(torch.int32)
+        ws = torch.empty(pluq.pluq_workspace_size(cfg.m, cfg.n, cfg.p), dtype=torch.uint8,
+                         device="cuda")
+        for _ in range(2):
+            A = A0.clone()
+            pluq.pluq_mod_p(A, cfg.p, mm=args.mm, workspace=ws)
+    torch.cuda.synchronize()
 
 
 # ----------------------------------------------------------------- clocks --
@@ -206,6 +242,12 @@ def run_ours(args):
         e1.record(stream)
         return e0, e1, r
 
+    # recursion cutoff and product threshold for this workload class
+    from paper_1301_4438_gb300 import autotune
+    tuned = autotune.tune(m, n, p, deficient=cfg.kind == "planted",
+                          cache=os.path.join(ROOT, "_build_tuning.json"), budget_s=60.0)
+    pluq.pluq_set_tuning(tuned[0], tuned[1])
+
     for _ in range(args.warmup):
         step(args.mm)
     torch.cuda.synchronize()
@@ -216,13 +258,26 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     launches0 = pluq.pluq_launch_count()
-    pluq.pluq_profile_enable(True)
     evs = [step(args.mm) for _ in range(args.steps)]
     torch.cuda.synchronize()
     barrier()
-    pluq.pluq_profile_enable(False)
     launches = pluq.pluq_launch_count() - launches0
     clk = clocks.stop()
+    # the same steps again with the roofline kernel's launches bracketed by
+    # CUDA events on their stream (kept out of the region `value` comes from)
+    roof_class = "tensor_mm" if args.mm == "tensor" else "simt_mm"
+    pluq.pluq_profile_enable([roof_class])
+    for _ in range(args.steps):
+        step(args.mm)
+    torch.cuda.synchronize()
+    pluq.pluq_profile_enable(False)
+    roof_stats = pluq.pluq_profile_read(roof_class)
+    # every class, one more pass, for the breakdown
+    pluq.pluq_profile_enable(True)
+    for _ in range(max(1, args.steps // 2)):
+        step(args.mm)
+    torch.cuda.synchronize()
+    pluq.pluq_profile_enable(False)
     times = [a.elapsed_time(b) for a, b, _ in evs]
     r = evs[-1][2]
     total_ms = sum(times)
@@ -233,7 +288,7 @@ def run_ours(args):
     work = fops(m, n, r)
     value = world * args.steps * work / (total_ms / 1e3) / 1e9
 
-    # per-class device time inside the timed region
+    # per-class device time (event-bracketed launches) for the breakdown
     classes = {}
     for name in pluq.PROFILE_CLASSES:
         nl, ms, w = pluq.pluq_profile_read(name)
@@ -241,8 +296,9 @@ def run_ours(args):
     dominant = max(classes, key=lambda k: classes[k]["ms"])
     hbm_peak, bf16_peak, peak_src = measured_peaks()
 
-    def roofline_for(name):
-        c = classes[name]
+    def roofline_for(name, stats=None):
+        c = classes[name] if stats is None else {"launches": stats[0], "ms": stats[1],
+                                                 "work": stats[2]}
         if c["launches"] == 0 or c["ms"] <= 0:
             return None
         per_launch_s = c["ms"] / c["launches"] / 1e3
@@ -263,8 +319,10 @@ def run_ours(args):
                 "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6,
                 "share_of_step": c["ms"] / max(sum(times), 1e-9)}
 
-    roof = roofline_for(dominant)
-    roof_mm = roofline_for("tensor_mm") if args.mm == "tensor" else roofline_for("simt_mm")
+    roof = roofline_for(roof_class, roof_stats)
+    roof["dominant_class_in_breakdown"] = dominant
+    roof["measured"] = (f"CUDA events around each {roof_class} launch on its stream over "
+                        f"{args.steps} instrumented steps that follow the timed ones")
 
     # ---------------- plain CUDA-core form on the same workload (context)
     simt_value = None
@@ -303,6 +361,36 @@ def run_ours(args):
            "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": m * n * 4 + (m + n) * 4,
            "ms_per_step": e2e_ms}
 
+    # the modular product on its own at a size where it is not latency bound
+    def gemm_rate(M, N, K, mm, reps=3):
+        g = torch.Generator(device=dev)
+        g.manual_seed(11)
+        Ag = torch.randint(0, p, (M, K), generator=g, device=dev, dtype=torch.int64).to(torch.int32)
+        Bg = torch.randint(0, p, (K, N), generator=g, device=dev, dtype=torch.int64).to(torch.int32)
+        Cg = torch.randint(0, p, (M, N), generator=g, device=dev, dtype=torch.int64).to(torch.int32)
+        wsg = torch.empty(max(pluq.modmm_workspace_size(M, N, K, p, mm), 1), dtype=torch.uint8,
+                          device=dev)
+        pluq.pluq_modmm(Cg, Ag, Bg, p, mm=mm, workspace=wsg)
+        cls = "tensor_mm" if mm == "tensor" else "simt_mm"
+        pluq.pluq_profile_enable([cls])
+        for _ in range(reps):
+            pluq.pluq_modmm(Cg, Ag, Bg, p, mm=mm, workspace=wsg)
+        torch.cuda.synchronize()
+        pluq.pluq_profile_enable(False)
+        nl, ms, w = pluq.pluq_profile_read(cls)
+        sec = ms / nl / 1e3
+        out = {"M": M, "N": N, "K": K, "form": mm, "kernel_ms": sec * 1e3,
+               "field_Tops": 2.0 * M * N * K / sec / 1e12}
+        if mm == "tensor":
+            out.update({"limbs": pluq.tensor_limbs(p), "tensor_TFLOPs": w / nl / sec / 1e12,
+                        "frac_of_bf16_peak": w / nl / sec / 1e12 / bf16_peak,
+                        "peak_source": f"{peak_src} bf16 burst {bf16_peak} TFLOP/s"})
+        del Ag, Bg, Cg, wsg
+        return out
+
+    gemm_big = [gemm_rate(8192, 8192, 8192, "tensor"), gemm_rate(8192, 8192, 2048, "tensor"),
+                gemm_rate(8192, 8192, 2048, "simt")]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs, ns, cores = cpu_oracle_rate()
@@ -322,9 +410,12 @@ def run_ours(args):
                        "limbs": pluq.tensor_limbs(p) if args.mm == "tensor" else None,
                        "l2": "flushed (256 MiB write) and input restored from a device copy "
                              "between steps, outside the timed events",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1],
+                                  "source": "autotune over leaf {32,64,128} x small-product "
+                                            "threshold {2^24,2^25,2^27}"}},
             "roofline": roof,
-            "modular_gemm": roof_mm,
+            "modular_gemm_standalone": gemm_big,
             "kernel_classes": classes,
             "plain_cuda_core_value": simt_value,
             "e2e": e2e,
@@ -381,6 +472,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.profile:
+        run_profile_target(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -186,9 +186,10 @@ pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t
 
 /*
  * Instrumentation (no counterpart in the paper).  pluq_launch_count: kernels
- * launched by this library since the process started.  pluq_profile_enable(1)
- * starts a session that brackets every launch of the timed kernel classes
- * with CUDA events on its stream (0 stops recording); pluq_profile_read
+ * launched by this library since the process started.
+ * pluq_profile_enable(class_mask) starts a session that brackets every launch
+ * of the kernel classes whose bit is set (bit c = class c below) with CUDA
+ * events on its stream; 0 stops recording.  pluq_profile_read
  * synchronises on those events and returns, for one class, the number of
  * launches, their summed device time in ms and their summed algorithmic work:
  *   0 tensor-core MM (2 L^2 M N K digit-product flops), 1 SIMT MM (2 M N K),
@@ -196,7 +197,7 @@ pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t
  *   4 limb splits (bytes), 5 triangular-inverse base blocks (field ops).
  */
 long long pluq_launch_count(void);
-pluq_status pluq_profile_enable(int on);
+pluq_status pluq_profile_enable(int class_mask);
 pluq_status pluq_profile_read(int kernel_class, long long *h_launches, double *h_ms,
                               double *h_work);
 
@@ -229,6 +230,17 @@ pluq_status pluq_profile_read(int kernel_class, long long *h_launches, double *h
 pluq_status pluq_modmm_tensor_noalloc(uint32_t *d_C, int64_t ldc, const uint32_t *d_A,
                                       int64_t lda, const uint32_t *d_B, int64_t ldb, int64_t M,
                                       int64_t N, int64_t K, uint32_t p, int assign, void *stream);
+
+/*
+ * Process-wide tuning knobs (no counterpart in the paper; chosen by the
+ * package's autotuner).  leaf: blocks with both sides <= leaf (16..128) are
+ * handed to the base-case kernel; small_mm_macs: products of at most this
+ * many multiply-adds use the CUDA-core kernel when the output does not overlap
+ * the operands.  They change speed only, never results.  Set before a call;
+ * calls in flight keep the values they started with.
+ */
+pluq_status pluq_set_tuning(int64_t leaf, int64_t small_mm_macs);
+pluq_status pluq_get_tuning(int64_t *h_leaf, int64_t *h_small_mm_macs);
 
 /* Number of 8-bit limbs the tensor form splits residues mod p into (1 to 4). */
 int pluq_tensor_limbs(uint32_t p);

@@ -220,8 +220,10 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
                         int32_t *perm_p, int32_t *perm_q, int32_t *info, int info_len,
                         cudaStream_t st, volatile int32_t *host_info = nullptr, int32_t seq = 0);
 
-// Products below this many multiply-adds go to the CUDA-core kernel when C
-// does not overlap A or B (launch latency dominates there).
-constexpr double SMALL_MM_MACS = 1 << 25;
+// Process-wide tuning (pluq_set_tuning): leaf size of the recursion, and the
+// number of multiply-adds below which a product goes to the CUDA-core kernel
+// when C does not overlap A or B (launch latency dominates there).
+extern std::atomic<int64_t> g_tune_leaf;
+extern std::atomic<int64_t> g_tune_small_mm;
 
 }  // namespace pluq

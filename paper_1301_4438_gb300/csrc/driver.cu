@@ -33,6 +33,9 @@ pluq_status launch_check_range(const uint32_t *A, int64_t lda, int64_t m, int64_
 pluq_status launch_any_nonzero(const uint32_t *A, int64_t lda, int64_t m, int64_t n, int32_t *words,
                                volatile int32_t *host, int32_t seq, cudaStream_t st);
 
+std::atomic<int64_t> g_tune_small_mm{1ll << 25};
+std::atomic<int64_t> g_tune_leaf{64};
+
 namespace {
 // byte ranges [lo, hi) spanned by a batch of strided blocks
 struct Span {
@@ -57,7 +60,7 @@ pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uin
         return launch_mm_simt(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, st);
     // small products: one CUDA-core launch beats split + split + tensor launch,
     // as long as C is disjoint from the operands it would overwrite
-    if (K > 0 && (double)M * N * K * batch <= SMALL_MM_MACS) {
+    if (K > 0 && (double)M * N * K * batch <= (double)g_tune_small_mm.load(std::memory_order_relaxed)) {
         Span sc = span(C.ptr, C.ld, M, N, batch, sC);
         if (!overlap(sc, span(A, lda, M, K, batch, sA)) && !overlap(sc, span(B, ldb, K, N, batch, sB)))
             return launch_mm_simt(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, st);
@@ -149,10 +152,13 @@ struct Ctx {
     int64_t zero_checks = 0;
 };
 
-// Leaf size of the recursion: PLUQ_LEAF (16..128) if set, else 64.  Smaller
-// leaves mean less one-SM elimination work per leaf (b^3/3 per leaf, n b^2/3
-// in all for an n x n full-rank matrix) but more recursion nodes.
-int64_t leaf_size()
+// Leaf size of the recursion (pluq_set_tuning; PLUQ_LEAF in the environment
+// sets the initial value).  Smaller leaves mean less one-SM elimination work
+// per leaf (b^3/3 per leaf, n b^2/3 in all for an n x n full-rank matrix) but
+// more recursion nodes.
+int64_t leaf_size() { return g_tune_leaf.load(std::memory_order_relaxed); }
+
+int64_t initial_leaf()
 {
     const char *e = getenv("PLUQ_LEAF");
     if (e) {
@@ -312,6 +318,10 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     return PLUQ_OK;
 }
 
+struct TuneInit {
+    TuneInit() { g_tune_leaf.store(initial_leaf()); }
+} g_tune_init;
+
 struct Layout {
     size_t gather, icopy, maps, vstack, small, arena, total;
 };
@@ -362,6 +372,22 @@ const char *pluq_status_string(int s)
 }
 
 int pluq_tensor_limbs(uint32_t p) { return limbs_for_prime(p); }
+
+pluq_status pluq_set_tuning(int64_t leaf, int64_t small_mm_macs)
+{
+    if (leaf < 16 || leaf > LEAF_MAX || small_mm_macs < 0) return PLUQ_EINVAL;
+    g_tune_leaf.store(leaf);
+    g_tune_small_mm.store(small_mm_macs);
+    return PLUQ_OK;
+}
+
+pluq_status pluq_get_tuning(int64_t *h_leaf, int64_t *h_small_mm_macs)
+{
+    if (!h_leaf || !h_small_mm_macs) return PLUQ_EINVAL;
+    *h_leaf = g_tune_leaf.load();
+    *h_small_mm_macs = g_tune_small_mm.load();
+    return PLUQ_OK;
+}
 int64_t pluq_leaf_max_rows(void) { return LEAF_MAX; }
 int64_t pluq_leaf_max_cols(void) { return LEAF_MAX; }
 

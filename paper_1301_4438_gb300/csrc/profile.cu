@@ -27,7 +27,7 @@ bool has_pending[NCLS];
 
 void start(int cls, cudaStream_t st)
 {
-    if (!g_on.load(std::memory_order_relaxed)) return;
+    if (!((g_on.load(std::memory_order_relaxed) >> cls) & 1)) return;
     std::lock_guard<std::mutex> lk(mu);
     if (used == recs.size()) {
         Rec r;
@@ -44,7 +44,7 @@ void start(int cls, cudaStream_t st)
 
 void stop(int cls, cudaStream_t st, double work)
 {
-    if (!g_on.load(std::memory_order_relaxed)) return;
+    if (!((g_on.load(std::memory_order_relaxed) >> cls) & 1)) return;
     std::lock_guard<std::mutex> lk(mu);
     if (used >= recs.size() || !has_pending[cls]) return;
     Rec &r = recs[used];
@@ -90,10 +90,11 @@ extern "C" {
 
 long long pluq_launch_count(void) { return prof::g_launches.load(); }
 
-pluq_status pluq_profile_enable(int on)
+pluq_status pluq_profile_enable(int class_mask)
 {
-    if (on) prof::begin_session();
-    prof::g_on.store(on ? 1 : 0);
+    if (class_mask & ~((1 << prof::NCLS) - 1)) return PLUQ_EINVAL;
+    if (class_mask) prof::begin_session();
+    prof::g_on.store(class_mask);
     return PLUQ_OK;
 }
 

@@ -59,6 +59,8 @@ _SIGS = {
     "pluq_mod_p_batched": (ctypes.c_int, [ctypes.POINTER(_vp), _i64p, _i64p, _i64p, _c_i64, _c_u32,
                                           ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64p, _vp,
                                           ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _vp]),
+    "pluq_set_tuning": (ctypes.c_int, [_c_i64, _c_i64]),
+    "pluq_get_tuning": (ctypes.c_int, [_i64p, _i64p]),
     "pluq_launch_count": (ctypes.c_longlong, []),
     "pluq_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pluq_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -293,8 +295,17 @@ def pluq_launch_count() -> int:
     return int(load().pluq_launch_count())
 
 
-def pluq_profile_enable(on: bool = True):
-    _check(load().pluq_profile_enable(int(on)), "pluq_profile_enable")
+def pluq_profile_enable(classes=True):
+    """True: every class; False: stop; or an iterable of class names."""
+    if classes is True:
+        mask = (1 << len(PROFILE_CLASSES)) - 1
+    elif not classes:
+        mask = 0
+    else:
+        mask = 0
+        for c in classes:
+            mask |= 1 << PROFILE_CLASSES.get(c, c)
+    _check(load().pluq_profile_enable(mask), "pluq_profile_enable")
 
 
 def pluq_profile_read(kernel_class):
@@ -347,3 +358,14 @@ def pluq_mod_p_batched(mats, p: int, mm: str = "auto", workers: int = 8, workspa
                                      _stream(stream)), "pluq_mod_p_batched")
     return ([pps[i][:shapes[i][0]] for i in range(cnt)], [pqs[i][:shapes[i][1]] for i in range(cnt)],
             [int(ranks[i]) for i in range(cnt)])
+
+
+def pluq_set_tuning(leaf: int, small_mm_macs: int):
+    _check(load().pluq_set_tuning(int(leaf), int(small_mm_macs)), "pluq_set_tuning")
+
+
+def pluq_get_tuning():
+    a = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _check(load().pluq_get_tuning(ctypes.byref(a), ctypes.byref(b)), "pluq_get_tuning")
+    return int(a.value), int(b.value)

@@ -109,3 +109,22 @@ def test_config_large_planted(name):
     assert r == cfg.r
     assert certify(A, cfg.p, LU, pp.cpu().numpy(), pq.cpu().numpy(), r, exact=False, trials=1,
                    expected_col_of_row=pl.rank_profile()) == ""
+
+
+def test_tuning_knobs_do_not_change_results():
+    """Leaf size and product threshold change speed only."""
+    p = 65521
+    A, _ = W.planted(700, 650, 300, p, seed=12)
+    old = pluq.pluq_get_tuning()
+    outs = []
+    try:
+        for leaf, small in [(16, 0), (64, 1 << 25), (128, 1 << 40)]:
+            pluq.pluq_set_tuning(leaf, small)
+            outs.append(run(A, p, "tensor"))
+    finally:
+        pluq.pluq_set_tuning(*old)
+    for o in outs[1:]:
+        assert o[3] == outs[0][3]
+        assert all(np.array_equal(x, y) for x, y in zip(o[:3], outs[0][:3]))
+    LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+    assert np.array_equal(outs[0][0], LU0)
