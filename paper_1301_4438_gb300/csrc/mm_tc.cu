@@ -12,15 +12,26 @@
 //     bounds the number of terms per accumulator so that every partial sum
 //     stays an integer of magnitude <= 2^24: fp32 holds it exactly whatever
 //     the order of summation;
-//   * after each chunk the epilogue warps drain TMEM, recombine
-//     sum_s acc_s 256^s in 64-bit integers, reduce once mod p (the delayed
-//     reduction of Sec. 5) and keep a running residue in spare TMEM columns;
-//     after the last chunk they apply C <- C - AB (or the assign forms).
-// One CTA computes a 128 x BN tile: warp 0 issues TMA loads (128B-swizzled
-// K-major tiles) into a ring of shared-memory stages, one thread of warp 1
-// issues the MMAs, warps 2-5 run the epilogue.  Every wait is bounded; a wait
-// that gives up raises an error word and the kernel winds down.
+//   * each stage's MMAs for one A digit plane i run against the L B planes
+//     stacked along N (one MMA of width L*BN), so block j of the result lands
+//     on accumulator i + j: L MMAs per 16-wide K step instead of L^2;
+//   * the CTA is persistent: it walks output tiles (grouped along M so that
+//     concurrent CTAs share A and B panels in L2) and keeps two accumulator
+//     sets in TMEM, so the MMAs of one K-chunk run while the epilogue warps
+//     drain the previous one;
+//   * the epilogue folds each chunk into a running residue kept in registers
+//     (the delayed reduction of Sec. 5: one reduction per chunk, not per
+//     product): for two limbs entirely in exact fp32 arithmetic, otherwise as
+//     one 64-bit dot product with the weights 256^s mod p and one Barrett
+//     reduction; after a tile's last chunk it applies C <- C - AB (or the
+//     assign forms) through shared memory, coalesced.
+// Warp 0 issues TMA loads (128B-swizzled K-major tiles) into a ring of
+// shared-memory stages, one thread of warp 1 issues the MMAs, warps 2-9 run
+// the epilogue.  Every wait is bounded; a wait that gives up raises an error
+// word and the kernel winds down after its own copies and MMAs have landed.
 #include <cuda.h>
+#include <algorithm>
+#include <climits>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -32,30 +43,32 @@ __device__ int g_tc_error = 0;
 namespace {
 
 constexpr int BM = 128, BK = 64;
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;          // TMA warp, MMA warp, 8 epilogue warps
+constexpr int EPI_WARPS = 8;
+constexpr int GROUP_M = 8;             // tile raster: GROUP_M row tiles per column sweep
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
+// Tile width BN: two accumulator sets of (2L-1) x BN fp32 columns fit in the
+// 512 TMEM columns; the stacked MMA is L*BN wide (at most 256).
+// KC_BLOCKS * 64 * (digit pairs per accumulator) * 2^14 <= 2^24.
 template <int L> struct Cfg;
-// KC_BLOCKS * 64 * (pairs per accumulator) * 2^14 <= 2^24
 template <> struct Cfg<1> { static constexpr int BN = 128, STAGES = 6, KC_BLOCKS = 16; };
-template <> struct Cfg<2> { static constexpr int BN = 128, STAGES = 3, KC_BLOCKS = 8; };
-template <> struct Cfg<3> { static constexpr int BN = 64, STAGES = 3, KC_BLOCKS = 5; };
-template <> struct Cfg<4> { static constexpr int BN = 64, STAGES = 2, KC_BLOCKS = 4; };
-
-constexpr int pow2_at_least(int x)
-{
-    int v = 32;
-    while (v < x) v <<= 1;
-    return v;
-}
+template <> struct Cfg<2> { static constexpr int BN = 80, STAGES = 4, KC_BLOCKS = 8; };
+template <> struct Cfg<3> { static constexpr int BN = 48, STAGES = 3, KC_BLOCKS = 5; };
+template <> struct Cfg<4> { static constexpr int BN = 32, STAGES = 2, KC_BLOCKS = 4; };
 
 template <int L> struct Geo {
     static constexpr int BN = Cfg<L>::BN, STAGES = Cfg<L>::STAGES, KCB = Cfg<L>::KC_BLOCKS;
     static constexpr int NACC = 2 * L - 1;
+    static constexpr int CW = BN / 2;   // columns per epilogue thread
     static constexpr uint32_t A_TILE = BM * BK * 2, B_TILE = BN * BK * 2;
     static constexpr uint32_t STAGE = L * (A_TILE + B_TILE);
-    static constexpr int TMEM_COLS = pow2_at_least(NACC * BN + BN);
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
+    static constexpr int TMEM_COLS = 512;
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + EPI_WARPS * 32 * 9 * 4;
+    static_assert(2 * NACC * BN <= TMEM_COLS, "two accumulator sets must fit in TMEM");
+    static_assert(L * BN <= 256 && BN % 16 == 0 && CW % 8 == 0, "MMA shape");
+    static_assert(B_TILE % 1024 == 0, "stacked B planes must keep the swizzle atom");
+    static_assert(SMEM <= 232448, "shared memory");
 };
 
 // ------------------------------------------------------------ PTX glue --
@@ -153,30 +166,15 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
 {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-        " [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0],"
-        " {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-        "r"(v[15])
-        : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // -------------------------------------------------------- limb splitting --
 template <int L>
@@ -213,7 +211,8 @@ __global__ void split_rows_kernel(const uint32_t *__restrict__ A, int64_t lda, i
     }
 }
 
-// B (K x N, row stride ldb) -> planes[(b*L + l)*Np + j][k] (transposed), zero padded.
+// B (K x N, row stride ldb) -> planes[(b*L + l)*Np + j][k] (transposed), zero padded;
+// Np is a multiple of the tile width, not necessarily of 32.
 template <int L>
 __global__ void split_cols_kernel(const uint32_t *__restrict__ B, int64_t ldb, int64_t sB, int K,
                                   int N, int64_t Np, int64_t Kp, uint32_t p,
@@ -238,7 +237,7 @@ __global__ void split_cols_kernel(const uint32_t *__restrict__ B, int64_t ldb, i
         const int64_t j = j0 + threadIdx.y + 8 * s, k = k0 + threadIdx.x;
 #pragma unroll
         for (int l = 0; l < L; ++l)
-            planes[((int64_t)(b * L + l) * Np + j) * Kp + k] = tile[l][threadIdx.x][threadIdx.y + 8 * s];
+            if (j < Np) planes[((int64_t)(b * L + l) * Np + j) * Kp + k] = tile[l][threadIdx.x][threadIdx.y + 8 * s];
     }
 }
 
@@ -248,29 +247,84 @@ struct TcArgs {
     int64_t ldc, sC;
     int M, N, nkb;
     int Mp, Np;
+    int ntm, ntn, ntiles;      // row tiles, column tiles, tiles over the whole batch
     int mode;
     Field F;
-    uint64_t off_lo, off_hi;   // multiples of p above the recombination bounds
-    uint32_t w32;              // 2^32 mod p
+    float pf, pinv;            // p and 1/p rounded to fp32 (two-limb recombination)
+    uint64_t off;              // multiple of p above the recombination bound (L != 2)
+    uint32_t w[7];             // 256^s mod p
 };
 
-template <int L>
-__device__ __forceinline__ uint32_t recombine(const float *acc, const TcArgs &a)
+// Chunk recombination, two limbs (257 < p < 2^17).  Every value below is an
+// integer held exactly in fp32 (magnitude < 2^24):
+//   fred(x): x - q p with q = rint(x * RN(1/p)), |result| <= 0.506 p;
+//   r_s = fred(acc_s); y = fred(r_1 + 256 r_2); run = fred(run + r_0 + 256 y).
+// |r_1 + 256 r_2| <= 257 * 0.506 p < 2^24 and the rint magic constant needs
+// |x / p| < 2^22, which holds for |x| <= 2^24 + 2^23 and p > 257.
+__device__ __forceinline__ float fred(float x, float pf, float pinv)
 {
-    // sum_s acc_s 256^s, s < 4 in one 64-bit word (< 2^49 in magnitude), s >= 4 in another
-    int64_t lo = 0, hi = 0;
+    const float M = 12582912.0f;   // 1.5 * 2^23: adding it rounds to an integer
+    const float q = __fsub_rn(__fmaf_rn(x, pinv, M), M);
+    return __fmaf_rn(-q, pf, x);
+}
+
+template <int L>
+__device__ __forceinline__ uint32_t chunk_update(const uint32_t (&raw)[2 * L - 1][8], int j,
+                                                 uint32_t run, bool first, const TcArgs &a)
+{
+    if constexpr (L == 2) {
+        const float r0 = fred(__uint_as_float(raw[0][j]), a.pf, a.pinv);
+        const float r1 = fred(__uint_as_float(raw[1][j]), a.pf, a.pinv);
+        const float r2 = fred(__uint_as_float(raw[2][j]), a.pf, a.pinv);
+        const float y = fred(__fmaf_rn(256.0f, r2, r1), a.pf, a.pinv);
+        float z = __fmaf_rn(256.0f, y, r0);
+        if (!first) z = __fadd_rn(z, __uint_as_float(run));
+        return __float_as_uint(fred(z, a.pf, a.pinv));
+    } else {
+        // sum_s acc_s (256^s mod p) + run + off: |acc_s| <= 2^24, so < 2^60
+        int64_t x = (int64_t)a.off + (first ? 0 : (int64_t)run);
 #pragma unroll
-    for (int s = 0; s < 2 * L - 1; ++s) {
-        int64_t v = (int64_t)__float2int_rn(acc[s]);
-        if (s < 4) lo += v * ((int64_t)1 << (8 * s));
-        else hi += v * ((int64_t)1 << (8 * (s - 4)));
+        for (int s = 0; s < 2 * L - 1; ++s)
+            x += (int64_t)__float2int_rn(__uint_as_float(raw[s][j])) * (int64_t)(int32_t)a.w[s];
+        return reduce64((uint64_t)x, a.F);
     }
-    uint32_t t = reduce64((uint64_t)(lo + (int64_t)a.off_lo), a.F);
-    if (2 * L - 1 > 4) {
-        uint32_t th = reduce64((uint64_t)(hi + (int64_t)a.off_hi), a.F);
-        t = add_mod(t, mul_mod(th, a.w32, a.F), a.F.p);
+}
+
+// running value after the last chunk -> residue in [0, p)
+template <int L>
+__device__ __forceinline__ uint32_t chunk_final(uint32_t run, uint32_t p)
+{
+    if constexpr (L == 2) {
+        const int v = __float2int_rn(__uint_as_float(run));   // |v| <= 0.506 p
+        return (uint32_t)(v < 0 ? v + (int)p : v);
+    } else {
+        return run;
     }
-    return t;
+}
+
+// Persistent tile order: GROUP_M row tiles are swept across all column tiles
+// before the next group, batch entries one after the other.
+template <int BN>
+__device__ __forceinline__ void tile_of(int t, const TcArgs &a, int &bz, int &m0, int &n0)
+{
+    const int per = a.ntm * a.ntn;
+    bz = t / per;
+    const int r = t - bz * per;
+    const int span = GROUP_M * a.ntn;
+    const int grp = r / span;
+    const int first = grp * GROUP_M;
+    const int gm = min(GROUP_M, a.ntm - first);
+    const int w = r - grp * span;
+    m0 = (first + w % gm) * BM;
+    n0 = (w / gm) * BN;
+}
+
+// wait used while winding down: bounded, ignores the abort word
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+        if (mbar_try(bar, parity)) return;
+    atomicExch(&g_tc_error, 1);
 }
 
 template <int L>
@@ -279,18 +333,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  TcArgs a)
 {
     using G = Geo<L>;
-    constexpr int BN = G::BN, STAGES = G::STAGES, KCB = G::KCB, NACC = G::NACC;
+    constexpr int BN = G::BN, STAGES = G::STAGES, KCB = G::KCB, NACC = G::NACC, CW = G::CW;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
     uint8_t *smem = smem_raw + (sbase - raw);
     uint64_t *bars = (uint64_t *)(smem + STAGES * G::STAGE);
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 2);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
     auto empty_bar = [&](int s) { return smem_u32(&bars[STAGES + s]); };
-    const uint32_t acc_full = smem_u32(&bars[2 * STAGES]);
-    const uint32_t acc_empty = smem_u32(&bars[2 * STAGES + 1]);
+    auto acc_full = [&](int b) { return smem_u32(&bars[2 * STAGES + b]); };
+    auto acc_empty = [&](int b) { return smem_u32(&bars[2 * STAGES + 2 + b]); };
+    const uint32_t mma_done = smem_u32(&bars[2 * STAGES + 4]);
+    // per epilogue warp: 32 x 8 words of C, rows padded to 9 words
+    uint32_t *stg_all = (uint32_t *)(smem + STAGES * G::STAGE + 256);
     auto a_tile = [&](int s, int l) { return sbase + s * G::STAGE + l * G::A_TILE; };
     auto b_tile = [&](int s, int l) { return sbase + s * G::STAGE + L * G::A_TILE + l * G::B_TILE; };
 
@@ -300,8 +357,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 128);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full(b), 1);
+            mbar_init(acc_empty(b), EPI_WARPS);
+        }
+        mbar_init(mma_done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -318,110 +378,197 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int bz = blockIdx.z;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nkb = a.nkb;
     const int nchunks = (nkb + KCB - 1) / KCB;
 
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (kb / STAGES) & 1;
-                if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag)) break;
-                mbar_expect_tx(full_bar(s), G::STAGE);
+            int s = 0;
+            uint32_t ph = 0, issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+                int bz, m0, n0;
+                tile_of<BN>(t, a, bz, m0, n0);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(full_bar(s), G::STAGE);
 #pragma unroll
-                for (int l = 0; l < L; ++l)
-                    tma_load_2d(a_tile(s, l), &mapA, kb * BK, (bz * L + l) * a.Mp + m0, full_bar(s));
+                    for (int l = 0; l < L; ++l)
+                        tma_load_2d(a_tile(s, l), &mapA, kb * BK, (bz * L + l) * a.Mp + m0, full_bar(s));
 #pragma unroll
-                for (int l = 0; l < L; ++l)
-                    tma_load_2d(b_tile(s, l), &mapB, kb * BK, (bz * L + l) * a.Np + n0, full_bar(s));
+                    for (int l = 0; l < L; ++l)
+                        tma_load_2d(b_tile(s, l), &mapB, kb * BK, (bz * L + l) * a.Np + n0, full_bar(s));
+                    ++issued;
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            // wind down: the copies of the last STAGES loads must have landed
+            for (uint32_t k = 0; k < (uint32_t)STAGES && k < issued; ++k) {
+                if (--s < 0) {
+                    s = STAGES - 1;
+                    ph ^= 1;
+                }
+                mbar_drain(full_bar(s), ph);
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
-            int kb = 0;
+            constexpr uint32_t ID_ALL = idesc_bf16(BM, L * BN);
+            constexpr uint32_t ID_LOW = idesc_bf16(BM, (L > 1 ? L - 1 : 1) * BN);
+            constexpr uint32_t ID_ONE = idesc_bf16(BM, BN);
+            int s = 0;
+            uint32_t ph = 0, cc = 0;
             bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                if (c > 0 && !mbar_wait(acc_empty, (c - 1) & 1, abort_flag)) break;
-                tc_fence_after();
-                uint32_t started = 0;
-                const int kend = min(nkb, (c + 1) * KCB);
-                for (; kb < kend; ++kb) {
-                    const int s = kb % STAGES;
-                    if (!mbar_wait(full_bar(s), (kb / STAGES) & 1, abort_flag)) {
+            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+                    const int buf = cc & 1;
+                    if (!mbar_wait(acc_empty(buf), ((cc >> 1) & 1) ^ 1, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    const uint32_t dacc = tmem + (uint32_t)(buf * NACC * BN);
+                    const int kend = min(nkb, (c + 1) * KCB);
+                    for (int kb = c * KCB; kb < kend; ++kb) {
+                        if (!mbar_wait(full_bar(s), ph, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
 #pragma unroll
-                    for (int i = 0; i < L; ++i)
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t db = sdesc(b_tile(s, 0) + kk * 32);
+                            const bool first = kb == c * KCB && kk == 0;
 #pragma unroll
-                        for (int j = 0; j < L; ++j) {
-                            const int acc = i + j;
-#pragma unroll
-                            for (int kk = 0; kk < BK / 16; ++kk) {
+                            for (int i = 0; i < L; ++i) {
+                                // A_i x [B_0 .. B_{L-1}] -> accumulators i .. i+L-1
                                 const uint64_t da = sdesc(a_tile(s, i) + kk * 32);
-                                const uint64_t db = sdesc(b_tile(s, j) + kk * 32);
-                                mma_bf16(tmem + acc * BN, da, db, idesc, (started >> acc) & 1);
-                                started |= 1u << acc;
+                                const uint32_t d = dacc + (uint32_t)(i * BN);
+                                if (!first) {
+                                    mma_bf16(d, da, db, ID_ALL, 1);
+                                } else if (i == 0) {
+                                    mma_bf16(d, da, db, ID_ALL, 0);
+                                } else {
+                                    // first step of a chunk: accumulator i+L-1 is fresh
+                                    mma_bf16(d, da, db, ID_LOW, 1);
+                                    mma_bf16(d + (uint32_t)((L - 1) * BN), da,
+                                             sdesc(b_tile(s, L - 1) + kk * 32), ID_ONE, 0);
+                                }
                             }
                         }
-                    mma_commit(empty_bar(s));
+                        mma_commit(empty_bar(s));
+                        if (++s == STAGES) {
+                            s = 0;
+                            ph ^= 1;
+                        }
+                    }
+                    if (ok) mma_commit(acc_full(buf));
                 }
-                if (ok) mma_commit(acc_full);
             }
+            // wind down: every MMA issued above has completed
+            mma_commit(mma_done);
+            mbar_drain(mma_done, 0);
         }
     } else {
-        // ---------------- epilogue: warps 2..5, TMEM lanes 32*(warp%4) ...
-        const int q = warp % 4;
-        const int row = q * 32 + lane;
-        const int grow = m0 + row;
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-        uint32_t *Cb = a.C + (int64_t)bz * a.sC;
+        // ---------------- epilogue: warps 2..9; TMEM lanes 32*(warp%4) ..,
+        // column half (warp-2)/4 of the tile
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * CW);
         const uint32_t p = a.F.p;
-        for (int c = 0; c < nchunks; ++c) {
-            if (!mbar_wait(acc_full, c & 1, abort_flag)) break;
-            tc_fence_after();
-            const bool last = c == nchunks - 1;
-#pragma unroll 1
-            for (int cs = 0; cs < BN; cs += 16) {
-                uint32_t raw_acc[NACC][16];
-#pragma unroll
-                for (int s = 0; s < NACC; ++s) tmem_ld16(tl + s * BN + cs, raw_acc[s]);
-                uint32_t run[16];
-                if (c > 0) tmem_ld16(tl + NACC * BN + cs, run);
-                tmem_wait_ld();
-                uint32_t t[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float acc[NACC];
-#pragma unroll
-                    for (int s = 0; s < NACC; ++s) acc[s] = __uint_as_float(raw_acc[s][j]);
-                    t[j] = recombine<L>(acc, a);
-                    if (c > 0) t[j] = add_mod(t[j], run[j], p);
+        uint32_t *stg = stg_all + (warp - 2) * 32 * 9;
+        uint32_t cc = 0;
+        bool ok = true;
+        uint32_t res[CW];
+        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+            int bz, m0, n0;
+            tile_of<BN>(t, a, bz, m0, n0);
+            for (int c = 0; c < nchunks; ++c, ++cc) {
+                const int buf = cc & 1;
+                if (!mbar_wait(acc_full(buf), (cc >> 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
                 }
-                if (!last) {
-                    tmem_st16(tl + NACC * BN + cs, t);
-                } else if (grow < a.M) {
-                    uint32_t *crow = Cb + (int64_t)grow * a.ldc + n0 + cs;
+                tc_fence_after();
+                const uint32_t tb = tl + (uint32_t)(buf * NACC * BN);
+                // TMEM loads of this thread's columns in flight together, in one
+                // group (or two, where the registers would not hold one)
+                constexpr int NSL = CW / 8, NGRP = L == 1 ? 4 : (L == 2 ? 2 : 1);
+                constexpr int GSL = (NSL + NGRP - 1) / NGRP;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (n0 + cs + j >= a.N) break;
-                        uint32_t out;
-                        if (a.mode == MM_SUB) out = sub_mod(crow[j], t[j], p);
-                        else if (a.mode == MM_ASSIGN) out = t[j];
-                        else out = t[j] == 0 ? 0u : p - t[j];
-                        crow[j] = out;
+                for (int g = 0; g < NGRP; ++g) {
+                    uint32_t rawv[GSL][NACC][8];
+#pragma unroll
+                    for (int k = 0; k < GSL; ++k)
+                        if (g * GSL + k < NSL)
+#pragma unroll
+                            for (int s = 0; s < NACC; ++s)
+                                tmem_ld8(tb + s * BN + (g * GSL + k) * 8, rawv[k][s]);
+                    tmem_wait_ld();
+                    if (g == NGRP - 1) {
+                        // accumulators read: hand the set back to the MMA issuer
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acc_empty(buf));
                     }
+#pragma unroll
+                    for (int k = 0; k < GSL; ++k)
+                        if (g * GSL + k < NSL)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int e = (g * GSL + k) * 8 + j;
+                                res[e] = chunk_update<L>(rawv[k], j, res[e], c == 0, a);
+                            }
                 }
             }
-            if (!last) tmem_wait_st();
-            tc_fence_before();
-            mbar_arrive(acc_empty);
+            if (!ok) break;
+            // C update, coalesced: each 32-row x 8-column block of this warp goes
+            // through shared memory so that a warp access covers 4 rows x 32
+            // bytes; all loads of C are in flight before the first store
+            const int col0 = n0 + half * CW;
+            const int rr = lane >> 3, cq = lane & 7;
+            const int grow0 = m0 + q * 32 + rr;
+            uint32_t *base = a.C + (int64_t)bz * a.sC + (int64_t)grow0 * a.ldc + col0 + cq;
+            const int64_t step = 4 * a.ldc;
+            const int rows_left = a.M - grow0;   // block row it is in range iff 4*it < rows_left
+            const int cols_left = a.N - col0 - cq;
+            uint32_t cv[CW];
+            if (a.mode == MM_SUB) {
+#pragma unroll
+                for (int sl = 0; sl < CW / 8; ++sl)
+#pragma unroll
+                    for (int it = 0; it < 8; ++it)
+                        cv[sl * 8 + it] = (sl * 8 < cols_left && 4 * it < rows_left)
+                                              ? base[it * step + sl * 8]
+                                              : 0u;
+            }
+#pragma unroll
+            for (int sl = 0; sl < CW / 8; ++sl) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) stg[lane * 9 + j] = chunk_final<L>(res[sl * 8 + j], p);
+                __syncwarp();
+                if (sl * 8 < cols_left) {
+#pragma unroll
+                    for (int it = 0; it < 8; ++it)
+                        if (4 * it < rows_left) {
+                            const uint32_t v = stg[(it * 4 + rr) * 9 + cq];
+                            uint32_t out;
+                            if (a.mode == MM_SUB) out = sub_mod(cv[sl * 8 + it], v, p);
+                            else if (a.mode == MM_ASSIGN) out = v;
+                            else out = v == 0 ? 0u : p - v;
+                            base[it * step + sl * 8] = out;
+                        }
+                }
+                __syncwarp();
+            }
         }
     }
 
@@ -469,7 +616,25 @@ bool make_map(CUtensorMap *map, void *base, int64_t rows, int64_t kp, int box_ro
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int bn_for(int L) { return L <= 2 ? 128 : 64; }
+int bn_for(int L)
+{
+    switch (L) {
+        case 1: return Cfg<1>::BN;
+        case 2: return Cfg<2>::BN;
+        case 3: return Cfg<3>::BN;
+        default: return Cfg<4>::BN;
+    }
+}
+
+// SMs of the current device (one persistent CTA each)
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        return 148;
+    return n;
+}
 
 template <int L>
 pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, int64_t M,
@@ -489,7 +654,7 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
     split_rows_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32), (unsigned)batch), blk, 0,
                            st>>>(A, lda, sA, (int)M, (int)K, Mp, Kp, p, pa);
     PLUQ_TRY(last_launch());
-    split_cols_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)(Np / 32), (unsigned)batch), blk, 0,
+    split_cols_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)ceil_div(Np, 32), (unsigned)batch), blk, 0,
                            st>>>(B, ldb, sB, (int)K, (int)N, Np, Kp, p, pb);
     PLUQ_TRY(last_launch());
     prof::stop(prof::SPLIT, st, (double)batch * ((M + N) * K * 4.0 + (Mp + Np) * Kp * 2.0 * L));
@@ -513,10 +678,20 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
     a.Np = (int)Np;
     a.mode = mode;
     a.F = F;
-    a.off_lo = ((1ull << 50) / p + 1) * p;
-    a.off_hi = ((1ull << 42) / p + 1) * p;
-    a.w32 = (uint32_t)((1ull << 32) % p);
-    dim3 grid((unsigned)(Np / G::BN), (unsigned)(Mp / BM), (unsigned)batch);
+    a.pf = (float)p;
+    a.pinv = 1.0f / (float)p;
+    a.off = ((uint64_t)(2 * L - 1) * (1ull << 24) + 1) * p;
+    uint64_t w = 1;
+    for (int s = 0; s < 7; ++s) {
+        a.w[s] = (uint32_t)w;
+        w = (w * 256) % p;
+    }
+    a.ntm = (int)(Mp / BM);
+    a.ntn = (int)(Np / G::BN);
+    const int64_t ntiles = (int64_t)a.ntm * a.ntn * batch;
+    if (ntiles > INT32_MAX) return PLUQ_EINVAL;
+    a.ntiles = (int)ntiles;
+    const int grid = (int)std::min<int64_t>(ntiles, sm_count());
     prof::start(prof::TC_MM, st);
     mm_tc_kernel<L><<<grid, NTHREADS, G::SMEM, st>>>(ma, mb, a);
     PLUQ_TRY(last_launch());
