@@ -128,6 +128,23 @@ pluq_status rank_profile_matrix(const int32_t *d_perm_p, const int32_t *d_perm_q
                                 int32_t *d_rows, int32_t *d_cols, void *stream);
 
 /*
+ * Factors of A = P [L; M] [U V] Q out of the packed result of pluq_mod_p
+ * (Sec. 2, the PLUQ form at the start of the algorithm's description), in the
+ * packed row / column order.  pluq_extract_L writes d_L (m x r, stride
+ * ldl >= r): the unit lower trapezoid [L; M] -- the strictly lower part of
+ * the first r packed columns, ones on the diagonal, zeros above it.
+ * pluq_extract_U writes d_U (r x n, stride ldu >= n): the upper trapezoid
+ * [U V] -- the first r packed rows on and above the diagonal, zeros below.
+ * d_LU is m x n with stride lda >= n and is not modified; the output must not
+ * overlap it.  Errors: EINVAL (sizes, r > min(m, n), null pointers with work
+ * to do).  Asynchronous on `stream`.
+ */
+pluq_status pluq_extract_L(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                           uint32_t *d_L, int64_t ldl, void *stream);
+pluq_status pluq_extract_U(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                           uint32_t *d_U, int64_t ldu, void *stream);
+
+/*
  * Hot-path kernels of Algorithm 1, callable on their own.
  *
  * MM(C, A, B) of Sec. 2: C <- C - A B mod p (or C <- A B mod p when `assign`

@@ -100,6 +100,38 @@ __device__ __forceinline__ uint32_t inv_mod(uint32_t a, uint32_t p)
 // (c = x or x - p, |c| <= p/2): c = sum_l d_l 256^l with d_l in [-128, 127]
 // for l < L-1 and |d_{L-1}| <= 128.  Every digit is an integer of magnitude
 // <= 128, exact in bf16, and a digit product is at most 2^14 in magnitude.
+// Primality of a 32-bit integer on the host: Miller-Rabin with the bases
+// 2, 7 and 61, which decides every n < 4,759,123,141 exactly (Jaeschke 1993).
+inline bool is_prime_u32(uint32_t n)
+{
+    if (n < 2) return false;
+    for (uint32_t q : {2u, 3u, 5u, 7u, 11u, 13u, 61u}) {
+        if (n == q) return true;
+        if (n % q == 0) return false;
+    }
+    uint32_t d = n - 1;
+    int s = 0;
+    while ((d & 1u) == 0) {
+        d >>= 1;
+        ++s;
+    }
+    for (uint64_t a : {2ull, 7ull, 61ull}) {
+        uint64_t x = 1, b = a % n;
+        for (uint32_t e = d; e; e >>= 1) {       // x = a^d mod n
+            if (e & 1u) x = x * b % n;
+            b = b * b % n;
+        }
+        if (x == 1 || x == n - 1) continue;
+        bool composite = true;
+        for (int i = 1; i < s && composite; ++i) {
+            x = x * x % n;
+            if (x == n - 1) composite = false;
+        }
+        if (composite) return false;
+    }
+    return true;
+}
+
 inline int limbs_for_prime(uint32_t p)
 {
     // smallest L with (p-1)/2 <= 128 (256^L - 1) / 255
@@ -210,6 +242,8 @@ pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, i
 size_t trsm_workspace(int64_t r, int64_t other, uint32_t p, int kind);
 
 pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st);
+pluq_status launch_extract(const uint32_t *LU, int64_t lda, int64_t rows, int64_t cols,
+                           uint32_t *X, int64_t ldx, bool lower, cudaStream_t st);
 
 // Leaf (base case) of the recursion.
 constexpr int LEAF_MAX = 128;

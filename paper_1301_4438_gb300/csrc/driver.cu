@@ -70,13 +70,6 @@ pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uin
 
 namespace {
 
-bool is_prime_u32(uint32_t p)
-{
-    if (p < 2) return false;
-    for (uint64_t d = 2; d * d <= p; ++d)
-        if (p % d == 0) return false;
-    return true;
-}
 
 // Mapped pinned host words: a kernel writes its result words and then a
 // sequence number there, and the host polls the sequence number instead of
@@ -122,18 +115,23 @@ void release_words(HostWords *w)
     g_words_free.push_back(w);
 }
 
-// wait for the leaf kernel to publish sequence number `seq` (bounded)
-pluq_status wait_words(HostWords *hw, int32_t seq, cudaStream_t st)
+// wait for a kernel to publish sequence number `seq` in host word `at`; the
+// stream is queried now and then so that a failed launch cannot hang the host
+pluq_status wait_words(HostWords *hw, int32_t seq, cudaStream_t st, int at = 0)
 {
     for (long long it = 0;; ++it) {
-        if (hw->h[0] == seq) return PLUQ_OK;
+        if (hw->h[at] == seq) return PLUQ_OK;
         if ((it & 0xFFFF) == 0xFFFF) {
             cudaError_t e = cudaStreamQuery(st);
-            if (e == cudaSuccess) return hw->h[0] == seq ? PLUQ_OK : PLUQ_EINTERNAL;
+            if (e == cudaSuccess) return hw->h[at] == seq ? PLUQ_OK : PLUQ_EINTERNAL;
             if (e != cudaErrorNotReady) return PLUQ_ECUDA;
         }
     }
 }
+
+// Host words 8 + 2d (sequence number) and 9 + 2d (flag) carry the zero test of
+// the node at recursion depth d < ZDEPTH; word 0..3 belong to the leaf.
+constexpr int ZBASE = 8, ZDEPTH = 27;
 
 struct Ctx {
     Field F;
@@ -212,7 +210,7 @@ bool in_order(const int64_t (*seg)[2], int count)
 // factorisation; pp / pq hold P / Q unless out.pid / out.qid say they are the
 // identity (then the vectors are not written).
 pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t *pp,
-                int32_t *pq, Res &out)
+                int32_t *pq, Res &out, int depth)
 {
     out = Res{};
     if (m == 0 || n == 0) return PLUQ_OK;
@@ -230,12 +228,20 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     }
     // A block's rank is the number of ones of R inside it, so deep in the
     // recursion of a rank-deficient matrix most blocks are exactly zero: one
-    // pass over the block prunes the whole subtree (r = 0, P = Q = I).
-    {
-        const int32_t seq = ++c.hw->seq;
-        PLUQ_TRY(launch_any_nonzero(A, lda, m, n, c.d_rank + 8, c.hw->d, seq, c.st));
-        PLUQ_TRY(wait_words(c.hw, seq, c.st));
-        ++c.zero_checks;
+    // pass over the block prunes the whole subtree (r = 0, P = Q = I).  The
+    // answer is read lazily: the descent into A1 goes ahead meanwhile and its
+    // first leaf (a synchronisation anyway) brings the answer along.  If the
+    // block is zero, so is A1, whose decomposition then changed nothing and
+    // reported r1 = 0 with identity permutations.
+    const bool lazy = depth < ZDEPTH;
+    const int32_t zseq = ++c.hw->seq;
+    const int zat = ZBASE + 2 * depth;
+    ++c.zero_checks;
+    if (lazy) {
+        PLUQ_TRY(launch_any_nonzero(A, lda, m, n, c.d_rank + 8, c.hw->d + zat, zseq, c.st));
+    } else {
+        PLUQ_TRY(launch_any_nonzero(A, lda, m, n, c.d_rank + 8, c.hw->d, zseq, c.st));
+        PLUQ_TRY(wait_words(c.hw, zseq, c.st));
         if (c.hw->h[1] == 0) return PLUQ_OK;
     }
     const int64_t k = m / 2, h = n / 2;
@@ -249,7 +255,15 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
 
     // A1 = P1 [L1;M1][U1 V1] Q1
     Res s1;
-    PLUQ_TRY(rec(c, A, k, h, lda, p1, q1, s1));
+    PLUQ_TRY(rec(c, A, k, h, lda, p1, q1, s1, depth + 1));
+    if (lazy) {
+        PLUQ_TRY(wait_words(c.hw, zseq, c.st, zat));
+        if (c.hw->h[zat + 1] == 0) {
+            if (s1.r != 0 || !s1.pid || !s1.qid) return PLUQ_EINTERNAL;
+            c.vtop = vmark;
+            return PLUQ_OK;
+        }
+    }
     const int64_t r1 = s1.r;
     // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
     PLUQ_TRY(permute_block(c, at(0, h), lda, k, n - h, vec(p1, s1.pid), nullptr));
@@ -264,8 +278,8 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
                        r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
     Res s2, s3;
-    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2));
-    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, s3));
+    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1));
+    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1));
     const int64_t r2 = s2.r, r3 = s3.r;
     int32_t *P2 = vec(p2, s2.pid), *Q2 = vec(q2, s2.qid), *P3 = vec(p3, s3.pid), *Q3 = vec(q3, s3.qid);
     // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
@@ -292,7 +306,7 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
                        lda, m - k - r3, n - h - r2, r3, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     // R = P4 [L4;M4][U4 V4] Q4
     Res s4;
-    PLUQ_TRY(rec(c, at(k + r3, h + r2), m - k - r3, n - h - r2, lda, p4, q4, s4));
+    PLUQ_TRY(rec(c, at(k + r3, h + r2), m - k - r3, n - h - r2, lda, p4, q4, s4, depth + 1));
     const int64_t r4 = s4.r;
     int32_t *P4 = vec(p4, s4.pid), *Q4 = vec(q4, s4.qid);
     // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T
@@ -446,7 +460,7 @@ pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p
     if (flag != 0) return PLUQ_ERANGE;
 
     Res res;
-    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res));
+    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res, 0));
     if (res.pid) PLUQ_TRY(launch_iota(d_perm_p, m, st));
     if (res.qid) PLUQ_TRY(launch_iota(d_perm_q, n, st));
     PLUQ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -600,6 +614,22 @@ pluq_status rank_profile_matrix(const int32_t *d_perm_p, const int32_t *d_perm_q
     if (r < 0 || r > m || r > n) return PLUQ_EINVAL;
     if (r > 0 && (!d_perm_p || !d_perm_q || !d_rows || !d_cols)) return PLUQ_EINVAL;
     return launch_rank_sort(d_perm_p, d_perm_q, r, d_rows, d_cols, (cudaStream_t)stream);
+}
+
+pluq_status pluq_extract_L(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                           uint32_t *d_L, int64_t ldl, void *stream)
+{
+    if (m < 0 || n < 0 || r < 0 || r > m || r > n || lda < n) return PLUQ_EINVAL;
+    if (m > 0 && r > 0 && (!d_LU || !d_L || ldl < r)) return PLUQ_EINVAL;
+    return launch_extract(d_LU, lda, m, r, d_L, ldl, true, (cudaStream_t)stream);
+}
+
+pluq_status pluq_extract_U(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                           uint32_t *d_U, int64_t ldu, void *stream)
+{
+    if (m < 0 || n < 0 || r < 0 || r > m || r > n || lda < n) return PLUQ_EINVAL;
+    if (n > 0 && r > 0 && (!d_LU || !d_U || ldu < n)) return PLUQ_EINVAL;
+    return launch_extract(d_LU, lda, r, n, d_U, ldu, false, (cudaStream_t)stream);
 }
 
 pluq_status pluq_modmm_workspace_size(int64_t M, int64_t N, int64_t K, uint32_t p, int mm_kind,

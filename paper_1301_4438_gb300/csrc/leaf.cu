@@ -201,12 +201,39 @@ struct LeafShared {
     int32_t perm_p[LM], perm_q[LM];
     uint32_t dval[LM], inv_d[LM], cval[LM], inv_c[LM];
     Frame stk[MAX_DEPTH];
+    unsigned long long step_bar;         // phase k completes when every warp has offered its step-k candidate
     int key[3];
     int r;
     int same;
+    int abort;
 };
 
 constexpr int NOKEY = 0x7FFFFFFF;
+constexpr uint32_t STEP_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Wait for phase `parity` of the step barrier (bounded; false if this or
+// another warp gave up).
+__device__ __forceinline__ bool step_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    for (uint32_t it = 0; it < STEP_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 63) == 63 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
 constexpr int MAXC = LM / 32;  // column slots per lane for the widest block
 
 // (d w - f q) mod p
@@ -302,7 +329,12 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
         S.col_of_row[i] = -1;
         S.row_of_col[i] = -1;
     }
-    if (tid == 0) S.key[0] = NOKEY;
+    const uint32_t bar = smem_addr(&S.step_bar);
+    if (tid == 0) {
+        S.key[0] = NOKEY;
+        S.abort = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(LT / 32) : "memory");
+    }
     uint32_t live = 0;   // bit s: column lane + 32 s is not a pivot column yet
 #pragma unroll
     for (int s = 0; s < CPL; ++s)
@@ -313,71 +345,66 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     __syncthreads();
 
     // ---------------- phase 1: row-order fraction-free elimination --------
-    // Step t: rows below the last pivot row are updated in registers; each
-    // warp offers its first row (at or below the pivot row + 1) with a live
-    // nonzero, publishing the row itself in cand[t & 1][warp]; key[t % 3]
-    // takes the block-wide minimum (row, column).  key[(t+1) % 3] is cleared
-    // during step t: every read of it happened before the previous barrier
-    // and every write comes after the next one.
+    // Step t: rows below the last pivot row are updated in registers, in row
+    // order.  A warp's first row (at or below the pivot row + 1) with a live
+    // nonzero is its candidate: as soon as it is known, the warp publishes the
+    // row in cand[t & 1][warp], takes key[t % 3] down to (row, column) and
+    // arrives on the step barrier; then it updates its remaining rows.  So a
+    // step waits for every warp's first candidate row, not for all updates.
+    // key[(t+1) % 3] is cleared during step t: every read of it happened before
+    // the previous phase completed and every write comes after this one.
     int r = 0, pi = -1, pc = 0, win = 0;
     uint32_t d = 0;
+    bool failed = false;
     for (int step = 0;; ++step) {
         if (tid == 0) S.key[(step + 1) % 3] = NOKEY;
         const int t0 = pi < warp ? 0 : (pi - warp) / NW + 1;   // first own row below pi
+        uint32_t prow[CPL];
         if (pi >= 0) {
-            uint32_t prow[CPL];
 #pragma unroll
             for (int s = 0; s < CPL; ++s)
                 if (s < ncl) prow[s] = S.cand[(step - 1) & 1][win][lane + 32 * s];
-            const int spc = pc >> 5, lpc = pc & 31;
-#pragma unroll
-            for (int t = 0; t < RPW; ++t) {
-                if (t < t0) continue;
-                if (t >= tmax) break;
-                const uint32_t f = __shfl_sync(0xFFFFFFFFu, pick<CPL>(w[t], spc), lpc);
-                if (f != 0) {
-#pragma unroll
-                    for (int s = 0; s < CPL; ++s)
-                        if (s < ncl && ((live >> s) & 1))
-                            w[t][s] = ff_update<SMALLP>(d, w[t][s], f, prow[s], F, F32);
-                } else if (d != 1) {
-#pragma unroll
-                    for (int s = 0; s < CPL; ++s)
-                        if (s < ncl && ((live >> s) & 1)) w[t][s] = scale<SMALLP>(d, w[t][s], F, F32);
-                }
-            }
         }
-        // this warp's first candidate row: OR of the lanes' row masks, then
-        // the smallest live nonzero column of that row
-        unsigned rows_nz = 0;
+        const int spc = pc >> 5, lpc = pc & 31;
+        bool offered = false;
 #pragma unroll
         for (int t = 0; t < RPW; ++t) {
             if (t < t0) continue;
             if (t >= tmax) break;
-            bool nz = false;
+            if (pi >= 0) {
+                // d w - f q also covers f = 0 (then it scales by d): no branch
+                const uint32_t f = __shfl_sync(0xFFFFFFFFu, pick<CPL>(w[t], spc), lpc);
 #pragma unroll
-            for (int s = 0; s < CPL; ++s)
-                if (s < ncl) nz |= ((live >> s) & 1) && w[t][s] != 0;
-            rows_nz |= (unsigned)nz << t;
-        }
-        rows_nz = __reduce_or_sync(0xFFFFFFFFu, rows_nz);
-        if (rows_nz) {
-            const int ct = __ffs(rows_nz) - 1;
-            int best = NOKEY;
+                for (int s = 0; s < CPL; ++s)
+                    if (s < ncl && ((live >> s) & 1))
+                        w[t][s] = ff_update<SMALLP>(d, w[t][s], f, prow[s], F, F32);
+            }
+            if (!offered) {
+                int best = NOKEY;
 #pragma unroll
-            for (int t = 0; t < RPW; ++t)
-                if (t == ct) {
-#pragma unroll
-                    for (int s = CPL - 1; s >= 0; --s)
-                        if (s < ncl && ((live >> s) & 1) && w[t][s] != 0) best = lane + 32 * s;
+                for (int s = CPL - 1; s >= 0; --s)
+                    if (s < ncl && ((live >> s) & 1) && w[t][s] != 0) best = lane + 32 * s;
+                best = __reduce_min_sync(0xFFFFFFFFu, best);
+                if (best != NOKEY) {
 #pragma unroll
                     for (int s = 0; s < CPL; ++s)
                         if (s < ncl) S.cand[step & 1][warp][lane + 32 * s] = w[t][s];
+                    if (lane == 0) atomicMin(&S.key[step % 3], (warp + NW * t) * LM + best);
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+                    offered = true;
                 }
-            best = __reduce_min_sync(0xFFFFFFFFu, best);
-            if (lane == 0) atomicMin(&S.key[step % 3], (warp + NW * ct) * LM + best);
+            }
         }
-        __syncthreads();
+        if (!offered) {
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+        }
+        if (!step_wait(bar, step & 1, &S.abort)) {
+            failed = true;
+            break;
+        }
         const int kv = S.key[step % 3];
         if (kv == NOKEY) break;
         pi = kv / LM;
@@ -393,6 +420,17 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
             S.row_of_col[pc] = pi;
         }
         ++r;
+    }
+    if (__syncthreads_or(failed)) {
+        if (tid == 0) {
+            info_out[0] = -1;
+            if (host_info) {
+                host_info[1] = -1;
+                __threadfence_system();
+                host_info[0] = seq;
+            }
+        }
+        return;
     }
 
     // ---------------- phase 2: Algorithm 1's order of the pivots ----------

@@ -190,54 +190,61 @@ __device__ __forceinline__ void to_digits(uint32_t x, uint32_t p, __nv_bfloat16 
     d[L - 1] = __float2bfloat16_rn((float)c);
 }
 
-// A (M x K, row stride lda) -> planes[(b*L + l)*Mp + i][k], zero padded.
+// One launch splits both operands.  Block rows y < Mp/32 take A (M x K, row
+// stride lda) -> planes_a[(b*L + l)*Mp + i][k]; the others take B (K x N, row
+// stride ldb) -> planes_b[(b*L + l)*Np + j][k], transposed through shared
+// memory.  Both zero padded; Np is a multiple of the tile width, not
+// necessarily of 32.
 template <int L>
-__global__ void split_rows_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t sA, int M,
-                                  int K, int64_t Mp, int64_t Kp, uint32_t p,
-                                  __nv_bfloat16 *__restrict__ planes)
-{
-    const int b = blockIdx.z;
-    const int64_t k = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t i0 = (int64_t)blockIdx.y * 32;
-    A += b * sA;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int64_t i = i0 + threadIdx.y + 8 * s;
-        uint32_t x = (i < M && k < K) ? A[i * lda + k] : 0u;
-        __nv_bfloat16 d[L];
-        to_digits<L>(x, p, d);
-#pragma unroll
-        for (int l = 0; l < L; ++l) planes[((int64_t)(b * L + l) * Mp + i) * Kp + k] = d[l];
-    }
-}
-
-// B (K x N, row stride ldb) -> planes[(b*L + l)*Np + j][k] (transposed), zero padded;
-// Np is a multiple of the tile width, not necessarily of 32.
-template <int L>
-__global__ void split_cols_kernel(const uint32_t *__restrict__ B, int64_t ldb, int64_t sB, int K,
-                                  int N, int64_t Np, int64_t Kp, uint32_t p,
-                                  __nv_bfloat16 *__restrict__ planes)
+__global__ void split_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t sA, int M,
+                             const uint32_t *__restrict__ B, int64_t ldb, int64_t sB, int N, int K,
+                             int64_t Mp, int64_t Np, int64_t Kp, uint32_t p,
+                             __nv_bfloat16 *__restrict__ planes_a,
+                             __nv_bfloat16 *__restrict__ planes_b)
 {
     __shared__ __nv_bfloat16 tile[L][32][33];
     const int b = blockIdx.z;
-    const int64_t k0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    const int64_t ya = Mp / 32, ytot = ya + (Np + 31) / 32;
+    A += b * sA;
     B += b * sB;
+    for (int64_t by = blockIdx.y; by < ytot; by += gridDim.y) {
+        if (by < ya) {
+            const int64_t k = k0 + threadIdx.x;
+            const int64_t i0 = by * 32;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int64_t k = k0 + threadIdx.y + 8 * s, j = j0 + threadIdx.x;
-        uint32_t x = (k < K && j < N) ? B[k * ldb + j] : 0u;
-        __nv_bfloat16 d[L];
-        to_digits<L>(x, p, d);
+            for (int s = 0; s < 4; ++s) {
+                const int64_t i = i0 + threadIdx.y + 8 * s;
+                uint32_t x = (i < M && k < K) ? A[i * lda + k] : 0u;
+                __nv_bfloat16 d[L];
+                to_digits<L>(x, p, d);
 #pragma unroll
-        for (int l = 0; l < L; ++l) tile[l][threadIdx.y + 8 * s][threadIdx.x] = d[l];
-    }
-    __syncthreads();
+                for (int l = 0; l < L; ++l)
+                    planes_a[((int64_t)(b * L + l) * Mp + i) * Kp + k] = d[l];
+            }
+            continue;
+        }
+        const int64_t j0 = (by - ya) * 32;
+        __syncthreads();   // the previous round's reads of the tile are done
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int64_t j = j0 + threadIdx.y + 8 * s, k = k0 + threadIdx.x;
+        for (int s = 0; s < 4; ++s) {
+            const int64_t k = k0 + threadIdx.y + 8 * s, j = j0 + threadIdx.x;
+            uint32_t x = (k < K && j < N) ? B[k * ldb + j] : 0u;
+            __nv_bfloat16 d[L];
+            to_digits<L>(x, p, d);
 #pragma unroll
-        for (int l = 0; l < L; ++l)
-            if (j < Np) planes[((int64_t)(b * L + l) * Np + j) * Kp + k] = tile[l][threadIdx.x][threadIdx.y + 8 * s];
+            for (int l = 0; l < L; ++l) tile[l][threadIdx.y + 8 * s][threadIdx.x] = d[l];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int64_t j = j0 + threadIdx.y + 8 * s, k = k0 + threadIdx.x;
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+                if (j < Np)
+                    planes_b[((int64_t)(b * L + l) * Np + j) * Kp + k] =
+                        tile[l][threadIdx.x][threadIdx.y + 8 * s];
+        }
     }
 }
 
@@ -651,11 +658,10 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
     const uint32_t p = F.p;
     dim3 blk(32, 8);
     prof::start(prof::SPLIT, st);
-    split_rows_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)(Mp / 32), (unsigned)batch), blk, 0,
-                           st>>>(A, lda, sA, (int)M, (int)K, Mp, Kp, p, pa);
-    PLUQ_TRY(last_launch());
-    split_cols_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)ceil_div(Np, 32), (unsigned)batch), blk, 0,
-                           st>>>(B, ldb, sB, (int)K, (int)N, Np, Kp, p, pb);
+    const int64_t ysplit = std::min<int64_t>(Mp / 32 + ceil_div(Np, 32), 65535);
+    split_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)ysplit, (unsigned)batch),
+                      blk, 0, st>>>(A, lda, sA, (int)M, B, ldb, sB, (int)N, (int)K, Mp, Np, Kp, p,
+                                    pa, pb);
     PLUQ_TRY(last_launch());
     prof::stop(prof::SPLIT, st, (double)batch * ((M + N) * K * 4.0 + (Mp + Np) * Kp * 2.0 * L));
 
@@ -766,9 +772,7 @@ extern "C" pluq_status pluq_modmm_tensor_noalloc(uint32_t *d_C, int64_t ldc, con
 {
     using namespace pluq;
     if (M < 0 || N < 0 || K < 0) return PLUQ_EINVAL;
-    if (p < 2 || p >= 0x80000000u) return PLUQ_ENOTPRIME;
-    for (uint64_t d = 2; d * d <= p; ++d)
-        if (p % d == 0) return PLUQ_ENOTPRIME;
+    if (p >= 0x80000000u || !is_prime_u32(p)) return PLUQ_ENOTPRIME;
     if (M > 0 && N > 0 && (!d_C || ldc < N)) return PLUQ_EINVAL;
     if (M > 0 && K > 0 && (!d_A || lda < K)) return PLUQ_EINVAL;
     if (K > 0 && N > 0 && (!d_B || ldb < N)) return PLUQ_EINVAL;

@@ -135,6 +135,25 @@ __global__ void check_range_kernel(const uint32_t *__restrict__ A, int64_t lda, 
         }
 }
 
+// Factor read-out from the packed [L\U V; M 0] (Sec. 2): `lower` writes the
+// rows x r unit lower trapezoid [L; M] (ones on the diagonal, zeros above),
+// otherwise the r x cols upper trapezoid [U V] (zeros below the diagonal).
+__global__ void extract_kernel(const uint32_t *__restrict__ LU, int64_t lda, int64_t rows,
+                               int64_t cols, uint32_t *__restrict__ X, int64_t ldx, int lower)
+{
+    const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
+    for (int64_t i = blockIdx.y; i < rows; i += gridDim.y)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int64_t j = c0 + (int64_t)s * GT;
+            if (j >= cols) continue;
+            uint32_t v;
+            if (lower) v = j < i ? LU[i * lda + j] : (j == i ? 1u : 0u);
+            else v = j >= i ? LU[i * lda + j] : 0u;
+            X[i * ldx + j] = v;
+        }
+}
+
 // Any nonzero in the m x n block?  Blocks OR their finding into words[0] and
 // count themselves in words[1]; the last block publishes the answer to the
 // mapped host words (flag, then sequence number) and clears both counters.
@@ -223,6 +242,14 @@ pluq_status launch_rank_sort(const int32_t *key, const int32_t *val, int64_t r, 
 {
     if (r <= 0) return PLUQ_OK;
     rank_sort_kernel<<<(unsigned)ceil_div(r, 256), 256, 0, st>>>(key, val, r, out_key, out_val);
+    return last_launch();
+}
+
+pluq_status launch_extract(const uint32_t *LU, int64_t lda, int64_t rows, int64_t cols,
+                           uint32_t *X, int64_t ldx, bool lower, cudaStream_t st)
+{
+    if (rows <= 0 || cols <= 0) return PLUQ_OK;
+    extract_kernel<<<grid2d(rows, cols), GT, 0, st>>>(LU, lda, rows, cols, X, ldx, lower ? 1 : 0);
     return last_launch();
 }
 

@@ -154,91 +154,173 @@ __global__ void __launch_bounds__(BT) inv_upper_base(const uint32_t *__restrict_
     }
 }
 
-// Direct solves for narrow triangles (r <= 64): one launch, the triangle and
-// the right-hand sides in shared memory, one thread per column (left) or row
-// (right) of B.  Each dot product is split over four independent running
-// sums; the code stays compact (a rolled loop), which matters more here than
-// unrolling.
-constexpr int DR = 64, DT = 64;
+// Direct solves for narrow triangles (r <= WR): one warp per right-hand side
+// (a column of B for the left solve, a row of B for the right one), lane q
+// owning triangle rows / columns q, q + 32, ...  The unknowns are produced one
+// per step: the owner of the next unknown finishes it and broadcasts it with a
+// shuffle, every lane adds its term into the running sums of its later rows.
+// The owner's sum over the earlier terms is reduced one step ahead, so a step's
+// dependency chain is one shuffle, one modular product and two subtractions.
+constexpr int WR = 128, WT = 256, WPB = WT / 32;
 
 template <bool SMALLP>
-__device__ __forceinline__ uint32_t dot4(const uint32_t *a, int astride, const uint32_t *b,
-                                         int bstride, int len, const Field &F, uint32_t w16)
+__device__ __forceinline__ uint32_t prod_mod(uint32_t a, uint32_t b, const Field &F,
+                                             const Field32 &F32)
 {
-    Acc<SMALLP> s0, s1, s2, s3;
-    int l = 0;
-    for (; l + 4 <= len; l += 4) {
-        s0.add(a[(l + 0) * astride], b[(l + 0) * bstride]);
-        s1.add(a[(l + 1) * astride], b[(l + 1) * bstride]);
-        s2.add(a[(l + 2) * astride], b[(l + 2) * bstride]);
-        s3.add(a[(l + 3) * astride], b[(l + 3) * bstride]);
-    }
-    for (; l < len; ++l) s0.add(a[l * astride], b[l * bstride]);
-    s0.lo += s1.lo + s2.lo + s3.lo;      // at most 64 products in all: no overflow
-    s0.hi += s1.hi + s2.hi + s3.hi;
-    return s0.value(F, w16);
+    if (SMALLP) return reduce32(a * b, F32);
+    return mul_mod(a, b, F);
 }
 
-// B (r x N) <- L^{-1} B, L unit lower; a block owns DT consecutive columns.
-template <bool SMALLP>
-__global__ void __launch_bounds__(DT) trsm_left_direct(const uint32_t *__restrict__ L, int64_t ldl,
-                                                        uint32_t *__restrict__ B, int64_t ldb,
-                                                        int r, int64_t N, Field F)
+template <int RPL, typename T>
+__device__ __forceinline__ T slot_pick(const T (&v)[RPL], int s)
 {
-    __shared__ uint32_t Ls[DR][DR + 1];
-    __shared__ uint32_t X[DR][DT];
-    const int64_t j0 = (int64_t)blockIdx.x * DT;
-    const int tx = threadIdx.x;
-#pragma unroll 16
-    for (int e = tx; e < r * r; e += DT) {
-        const int i = e / r, c = e % r;
-        Ls[i][c] = L[(int64_t)i * ldl + c];
-    }
-    const bool ok = j0 + tx < N;
-#pragma unroll 16
-    for (int i = 0; i < r; ++i) X[i][tx] = ok ? B[(int64_t)i * ldb + j0 + tx] : 0u;
-    __syncthreads();
-    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    for (int i = 1; i < r; ++i)
-        X[i][tx] = sub_mod(X[i][tx], dot4<SMALLP>(&Ls[i][0], 1, &X[0][tx], DT, i, F, w16), F.p);
-    if (ok)
-        for (int i = 0; i < r; ++i) B[(int64_t)i * ldb + j0 + tx] = X[i][tx];
+    T x = v[0];
+#pragma unroll
+    for (int t = 1; t < RPL; ++t)
+        if (s == t) x = v[t];
+    return x;
 }
 
-// B (M x r) <- B U^{-1}, U upper with nonzero diagonal; a block owns DT rows.
-template <bool SMALLP>
-__global__ void __launch_bounds__(DT) trsm_right_direct(const uint32_t *__restrict__ U, int64_t ldu,
-                                                         uint32_t *__restrict__ B, int64_t ldb,
-                                                         int64_t M, int r, Field F)
+// odd row stride of the staged triangle: a lane per row reads without conflicts
+__host__ __device__ __forceinline__ int tri_ld(int r) { return (r & 1) ? r + 2 : r + 1; }
+
+// B (r x N) <- L^{-1} B, L unit lower (diagonal not read).
+template <bool SMALLP, int RPL>
+__global__ void __launch_bounds__(WT) trsm_left_warp(const uint32_t *__restrict__ L, int64_t ldl,
+                                                      uint32_t *__restrict__ B, int64_t ldb, int r,
+                                                      int64_t N, Field F)
 {
-    __shared__ uint32_t Us[DR][DR + 1];
-    __shared__ uint32_t X[DT][DR + 1];
-    __shared__ uint32_t dinv[DR];
-    const int64_t i0 = (int64_t)blockIdx.x * DT;
-    const int tx = threadIdx.x;
-#pragma unroll 16
-    for (int e = tx; e < r * r; e += DT) {
+    extern __shared__ uint32_t Ls[];
+    const int ld = tri_ld(r);
+    for (int e = threadIdx.x; e < r * r; e += WT) {
         const int i = e / r, c = e % r;
-        Us[i][c] = U[(int64_t)i * ldu + c];
-    }
-#pragma unroll 16
-    for (int e = tx; e < DT * r; e += DT) {
-        const int i = e / r, c = e % r;
-        X[i][c] = i0 + i < M ? B[(i0 + i) * ldb + c] : 0u;
+        if (c < i) Ls[i * ld + c] = L[(int64_t)i * ldl + c];
     }
     __syncthreads();
-    if (tx < r) dinv[tx] = inv_mod(Us[tx][tx], F.p);
-    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (j >= N) return;
+    const Field32 F32{F.p, 0xFFFFFFFFu / F.p};
     const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    for (int j = 0; j < r; ++j) {
-        const uint32_t s = dot4<SMALLP>(&X[tx][0], 1, &Us[0][j], DR + 1, j, F, w16);
-        X[tx][j] = mul_mod(sub_mod(X[tx][j], s, F.p), dinv[j], F);
+    uint32_t b[RPL];
+    Acc<SMALLP> acc[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        b[t] = row < r ? B[(int64_t)row * ldb + j] : 0u;
+    }
+    uint32_t x = __shfl_sync(0xFFFFFFFFu, b[0], 0);   // x_0 = b_0
+    uint32_t vnext = 0;                               // owner's sum for row i + 1, terms < i
+    for (int i = 0; i + 1 < r; ++i) {
+        const int nr = i + 1, nl = nr & 31, ns = nr >> 5;
+        const uint32_t lx = Ls[nr * ld + i];
+        const uint32_t xn = sub_mod(sub_mod(slot_pick<RPL>(b, ns), vnext, F.p),
+                                    prod_mod<SMALLP>(lx, x, F, F32), F.p);
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int row = lane + 32 * t;
+            if (row > nr && row < r) acc[t].add(Ls[row * ld + i], x);
+            if (t == ns && lane == nl) b[t] = xn;
+        }
+        x = __shfl_sync(0xFFFFFFFFu, xn, nl);
+        vnext = slot_pick<RPL>(acc, (i + 2) >> 5).value(F, w16);
+    }
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        if (row < r) B[(int64_t)row * ldb + j] = b[t];
+    }
+}
+
+// B (M x r) <- B U^{-1}, U upper with nonzero diagonal.
+template <bool SMALLP, int RPL>
+__global__ void __launch_bounds__(WT) trsm_right_warp(const uint32_t *__restrict__ U, int64_t ldu,
+                                                       uint32_t *__restrict__ B, int64_t ldb,
+                                                       int64_t M, int r, Field F)
+{
+    extern __shared__ uint32_t Us[];
+    const int ld = tri_ld(r);
+    uint32_t *dinv = Us + r * ld;
+    for (int e = threadIdx.x; e < r * r; e += WT) {
+        const int i = e / r, c = e % r;
+        if (c >= i) Us[i * ld + c] = U[(int64_t)i * ldu + c];
     }
     __syncthreads();
-    for (int e = tx; e < DT * r; e += DT) {
-        const int i = e / r, c = e % r;
-        if (i0 + i < M) B[(i0 + i) * ldb + c] = X[i][c];
+    for (int t = threadIdx.x; t < r; t += WT) dinv[t] = inv_mod(Us[t * ld + t], F.p);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+    if (i >= M) return;
+    const Field32 F32{F.p, 0xFFFFFFFFu / F.p};
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    uint32_t b[RPL];
+    Acc<SMALLP> acc[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+        const int c = lane + 32 * t;
+        b[t] = c < r ? B[i * ldb + c] : 0u;
     }
+    uint32_t x = prod_mod<SMALLP>(__shfl_sync(0xFFFFFFFFu, b[0], 0), dinv[0], F, F32);
+    if (lane == 0) b[0] = x;
+    uint32_t vnext = 0;
+    for (int l = 0; l + 1 < r; ++l) {
+        const int nc = l + 1, nl = nc & 31, ns = nc >> 5;
+        const uint32_t ux = Us[l * ld + nc];
+        const uint32_t xn = prod_mod<SMALLP>(
+            sub_mod(sub_mod(slot_pick<RPL>(b, ns), vnext, F.p), prod_mod<SMALLP>(ux, x, F, F32),
+                    F.p),
+            dinv[nc], F, F32);
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int c = lane + 32 * t;
+            if (c > nc && c < r) acc[t].add(Us[l * ld + c], x);
+            if (t == ns && lane == nl) b[t] = xn;
+        }
+        x = __shfl_sync(0xFFFFFFFFu, xn, nl);
+        vnext = slot_pick<RPL>(acc, (l + 2) >> 5).value(F, w16);
+    }
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+        const int c = lane + 32 * t;
+        if (c < r) B[i * ldb + c] = b[t];
+    }
+}
+
+template <bool SMALLP, int RPL>
+pluq_status launch_trsm_warp(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_t other,
+                             int r, Field F, cudaStream_t st)
+{
+    const size_t smem = ((size_t)r * tri_ld(r) + (left ? 0 : r)) * sizeof(uint32_t);
+    const unsigned grid = (unsigned)ceil_div(other, WPB);
+    if (left) {
+        static const bool attr = cudaFuncSetAttribute(trsm_left_warp<SMALLP, RPL>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)(WR * tri_ld(WR) * 4)) == cudaSuccess;
+        if (!attr) return PLUQ_ECUDA;
+        trsm_left_warp<SMALLP, RPL><<<grid, WT, smem, st>>>(T, ldt, B.ptr, B.ld, r, other, F);
+    } else {
+        static const bool attr = cudaFuncSetAttribute(trsm_right_warp<SMALLP, RPL>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)((WR * tri_ld(WR) + WR) * 4)) == cudaSuccess;
+        if (!attr) return PLUQ_ECUDA;
+        trsm_right_warp<SMALLP, RPL><<<grid, WT, smem, st>>>(T, ldt, B.ptr, B.ld, other, r, F);
+    }
+    return last_launch();
+}
+
+pluq_status trsm_direct(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_t other, int r,
+                        Field F, cudaStream_t st)
+{
+    const bool sp = F.p <= 65536u;
+    const int rpl = r <= 32 ? 1 : r <= 64 ? 2 : 4;
+    if (sp) {
+        if (rpl == 1) return launch_trsm_warp<true, 1>(left, T, ldt, B, other, r, F, st);
+        if (rpl == 2) return launch_trsm_warp<true, 2>(left, T, ldt, B, other, r, F, st);
+        return launch_trsm_warp<true, 4>(left, T, ldt, B, other, r, F, st);
+    }
+    if (rpl == 1) return launch_trsm_warp<false, 1>(left, T, ldt, B, other, r, F, st);
+    if (rpl == 2) return launch_trsm_warp<false, 2>(left, T, ldt, B, other, r, F, st);
+    return launch_trsm_warp<false, 4>(left, T, ldt, B, other, r, F, st);
 }
 
 }  // namespace
@@ -348,13 +430,9 @@ pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t 
                                  Field F, int kind, Arena &ar, cudaStream_t st)
 {
     if (r <= 0 || N <= 0) return PLUQ_OK;
-    if (r <= DR) {
+    if (r <= WR) {
         prof::start(prof::TRI, st);
-        if (F.p <= 65536u)
-            trsm_left_direct<true><<<(unsigned)ceil_div(N, DT), DT, 0, st>>>(L, ldl, B.ptr, B.ld, (int)r, N, F);
-        else
-            trsm_left_direct<false><<<(unsigned)ceil_div(N, DT), DT, 0, st>>>(L, ldl, B.ptr, B.ld, (int)r, N, F);
-        pluq_status s = last_launch();
+        pluq_status s = trsm_direct(true, L, ldl, B, N, (int)r, F, st);
         prof::stop(prof::TRI, st, (double)r * r * N / 2.0);
         return s;
     }
@@ -379,13 +457,9 @@ pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, i
                              Field F, int kind, Arena &ar, cudaStream_t st)
 {
     if (r <= 0 || M <= 0) return PLUQ_OK;
-    if (r <= DR) {
+    if (r <= WR) {
         prof::start(prof::TRI, st);
-        if (F.p <= 65536u)
-            trsm_right_direct<true><<<(unsigned)ceil_div(M, DT), DT, 0, st>>>(U, ldu, B.ptr, B.ld, M, (int)r, F);
-        else
-            trsm_right_direct<false><<<(unsigned)ceil_div(M, DT), DT, 0, st>>>(U, ldu, B.ptr, B.ld, M, (int)r, F);
-        pluq_status s = last_launch();
+        pluq_status s = trsm_direct(false, U, ldu, B, M, (int)r, F, st);
         prof::stop(prof::TRI, st, (double)r * r * M / 2.0);
         return s;
     }

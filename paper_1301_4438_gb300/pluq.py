@@ -39,6 +39,8 @@ _SIGS = {
     "row_rank_profile": (ctypes.c_int, [_vp, _c_i64, _c_i64, _vp, _vp]),
     "col_rank_profile": (ctypes.c_int, [_vp, _c_i64, _c_i64, _vp, _vp]),
     "rank_profile_matrix": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp]),
+    "pluq_extract_L": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _c_i64, _vp]),
+    "pluq_extract_U": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _c_i64, _vp]),
     "pluq_modmm_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _c_u32, ctypes.c_int,
                                                  _szp]),
     "pluq_modmm": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _c_i64, _c_i64, _c_i64,
@@ -189,6 +191,26 @@ def rank_profile_matrix(perm_p: torch.Tensor, perm_q: torch.Tensor, r: int, stre
                                       r, _ptr(rows), _ptr(cols), _stream(stream)),
            "rank_profile_matrix")
     return rows[:r], cols[:r]
+
+
+def pluq_extract_L(LU: torch.Tensor, r: int, stream=None) -> torch.Tensor:
+    """[L; M] (m x r, unit lower trapezoid) from the packed result of pluq_mod_p."""
+    _need_cuda(LU)
+    m, n = LU.shape
+    L = torch.empty((m, max(r, 0)), dtype=LU.dtype, device=LU.device)
+    _check(load().pluq_extract_L(_ptr(LU), m, n, LU.stride(0), r, _ptr(L), max(r, 1),
+                                 _stream(stream)), "pluq_extract_L")
+    return L
+
+
+def pluq_extract_U(LU: torch.Tensor, r: int, stream=None) -> torch.Tensor:
+    """[U V] (r x n, upper trapezoid) from the packed result of pluq_mod_p."""
+    _need_cuda(LU)
+    m, n = LU.shape
+    U = torch.empty((max(r, 0), n), dtype=LU.dtype, device=LU.device)
+    _check(load().pluq_extract_U(_ptr(LU), m, n, LU.stride(0), r, _ptr(U), max(n, 1),
+                                 _stream(stream)), "pluq_extract_U")
+    return U
 
 
 def modmm_workspace_size(M: int, N: int, K: int, p: int, mm: str = "auto") -> int:

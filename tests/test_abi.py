@@ -52,3 +52,31 @@ def test_host_only_queries():
     import pytest
     with pytest.raises(pluq.PluqError):
         pluq.pluq_workspace_size(10, 10, 65535)     # not prime
+
+
+def test_modulus_validation_matches_trial_division():
+    """The library's primality test (Miller-Rabin, bases 2, 7, 61) against
+    trial division: small numbers, Carmichael numbers, strong pseudoprimes to
+    small bases and the neighbourhood of 2^31."""
+    import pytest
+
+    def trial(n):
+        if n < 2:
+            return False
+        d = 2
+        while d * d <= n:
+            if n % d == 0:
+                return False
+            d += 1
+        return True
+
+    cases = list(range(0, 2000)) + [561, 1105, 1729, 2465, 2821, 6601, 8911, 25326001,
+                                     3215031751 % (1 << 31), 2047, 1373653, 9080191,
+                                     4759123141 % (1 << 31), 65521, 65535, 65537, 8388593,
+                                     8388607] + list(range((1 << 31) - 300, 1 << 31))
+    for n in cases:
+        if trial(n):
+            assert pluq.pluq_workspace_size(4, 4, n) > 0, n
+        else:
+            with pytest.raises(pluq.PluqError):
+                pluq.pluq_workspace_size(4, 4, n)

@@ -132,7 +132,8 @@ def test_modmm_strided_blocks(kind):
 @pytest.mark.parametrize("p", [3, 65521, 2147483647])
 def test_trsm_matches_oracle(kind, p):
     g = np.random.Generator(np.random.PCG64(2000 + p))
-    for (r, other) in [(1, 5), (63, 10), (64, 64), (65, 200), (200, 130), (517, 300)]:
+    for (r, other) in [(1, 5), (2, 1), (31, 7), (32, 33), (63, 10), (64, 64), (65, 200), (96, 17),
+                       (127, 9), (128, 128), (129, 20), (200, 130), (517, 300)]:
         L = g.integers(0, p, (r, r)).astype(np.uint32)
         B = g.integers(0, p, (r, other)).astype(np.uint32)
         want = oracle.trsm_left_lower_unit(L, B, p)
@@ -179,6 +180,37 @@ def test_rank_profile_readouts():
     order = np.argsort(pl.rows)
     assert np.array_equal(rr.cpu().numpy(), pl.rows[order])
     assert np.array_equal(cc.cpu().numpy(), pl.cols[order])
+
+
+@pytest.mark.parametrize("m,n,r,p", [(300, 200, 120, 65521), (150, 260, 150, 65521),
+                                     (90, 70, 3, 2147483647), (40, 30, 0, 7)])
+def test_extract_factors(m, n, r, p):
+    """[L; M] and [U V] read out of the packed result: equal to the oracle's
+    packed factors sliced by definition, and P [L; M] [U V] Q == A."""
+    A, _ = W.planted(m, n, r, p, seed=m + n + r)
+    LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+    d = dev(A)
+    pp, pq, rk = pluq.pluq_mod_p(d, p, mm="tensor")
+    assert rk == r0 == r
+    L = pluq.pluq_extract_L(d, rk).cpu().numpy().astype(np.uint32)
+    U = pluq.pluq_extract_U(d, rk).cpu().numpy().astype(np.uint32)
+    L0 = np.tril(LU0[:, :r0].astype(np.int64), -1) + np.eye(m, r0, dtype=np.int64)
+    U0 = np.triu(LU0[:r0, :].astype(np.int64))
+    assert np.array_equal(L.astype(np.int64), L0)
+    assert np.array_equal(U.astype(np.int64), U0)
+    # reconstruction, exact in Python integers
+    prod = np.array(L, dtype=object).dot(np.array(U, dtype=object)) % p if r0 else \
+        np.zeros((m, n), dtype=object)
+    Ap = A[pp0][:, pq0].astype(object)
+    assert np.array_equal(prod, Ap)
+
+
+def test_extract_errors():
+    d = torch.zeros((4, 5), dtype=torch.int32, device="cuda")
+    with pytest.raises(pluq.PluqError):
+        pluq.pluq_extract_L(d, 5)          # r > min(m, n)
+    with pytest.raises(pluq.PluqError):
+        pluq.pluq_extract_U(d, -1)
 
 
 # -------------------------------------------------------------- errors --
