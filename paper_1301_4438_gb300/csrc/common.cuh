@@ -31,11 +31,17 @@ inline Field make_field(uint32_t p)
     return f;
 }
 
+// r mod p for r < 2p without a branch: when r < p, r - p wraps above r, so
+// the unsigned minimum picks r; otherwise it picks r - p.  (Conditional
+// subtractions written as ?: can turn into divergent branches, which
+// serialise the independent reductions of a warp.)
+__device__ __forceinline__ uint32_t fold(uint32_t r, uint32_t p) { return min(r, r - p); }
+
 __device__ __forceinline__ uint32_t reduce64(uint64_t x, const Field &F)
 {
-    uint64_t q = __umul64hi(x, F.mu);
-    uint64_t r = x - q * (uint64_t)F.p;
-    return (uint32_t)(r >= F.p ? r - F.p : r);
+    // q in {floor(x/p) - 1, floor(x/p)}, so x - q p < 2p < 2^32
+    const uint64_t q = __umul64hi(x, F.mu);
+    return fold((uint32_t)(x - q * (uint64_t)F.p), F.p);
 }
 
 __device__ __forceinline__ uint32_t mul_mod(uint32_t a, uint32_t b, const Field &F)
@@ -45,13 +51,14 @@ __device__ __forceinline__ uint32_t mul_mod(uint32_t a, uint32_t b, const Field 
 
 __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t p)
 {
-    uint32_t s = a + b;            // < 2^32 since a, b < 2^31
-    return s >= p ? s - p : s;
+    return fold(a + b, p);         // a + b < 2p < 2^32 since a, b < p < 2^31
 }
 
 __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t p)
 {
-    return a >= b ? a - b : a + (p - b);
+    // a - b wraps above 2^32 - p when a < b; adding p then lands in [1, p)
+    const uint32_t d = a - b;
+    return min(d, d + p);
 }
 
 // (a*b - c*d) mod p with one reduction: a*b + c*(p-d) < 2^63.
@@ -72,11 +79,22 @@ inline Field32 make_field32(uint32_t p) { return Field32{p, 0xFFFFFFFFu / p}; }
 
 __device__ __forceinline__ uint32_t reduce32(uint32_t x, const Field32 &F)
 {
-    uint32_t r = x - __umulhi(x, F.mu) * F.p;
-    return r >= F.p ? r - F.p : r;
+    return fold(x - __umulhi(x, F.mu) * F.p, F.p);
 }
 
 // Inverse of a nonzero residue by the extended Euclidean algorithm.
+// a^e mod p by square and multiply (a^(p-2) is the inverse of a != 0, Fermat)
+__device__ __forceinline__ uint32_t pow_mod(uint32_t a, uint32_t e, const Field &F)
+{
+    uint32_t x = 1;
+    while (e) {
+        if (e & 1u) x = mul_mod(x, a, F);
+        a = mul_mod(a, a, F);
+        e >>= 1;
+    }
+    return x;
+}
+
 __device__ __forceinline__ uint32_t inv_mod(uint32_t a, uint32_t p)
 {
     uint32_t r0 = p, r1 = a;

@@ -20,6 +20,12 @@
 //     of phase 2 equals the row order of phase 1 (always the case for generic
 //     rank profiles), phase 1 already holds this factorisation and phase 3 is
 //     skipped.
+// Before phase 1 the kernel tries the generic case: when every leading
+// principal minor of order <= min(m, n) is nonzero, R is the identity pattern
+// (rho(k, t) = min(k, t)), Algorithm 1 meets the pivots on the diagonal and
+// P = Q = I, so the result is the LU factorisation without pivoting.  It runs
+// blocked (see generic_lu) and hands over to the three phases at the first
+// zero pivot, before anything is written to global memory.
 // Both eliminations are fraction free: at pivot k with value d_k every active
 // row becomes d_k * row - row[pivot col] * pivot row, so no inverse sits on the
 // sequential path.  All active rows then carry the common factor
@@ -206,6 +212,7 @@ struct LeafShared {
     int r;
     int same;
     int abort;
+    int gfail;
 };
 
 constexpr int NOKEY = 0x7FFFFFFF;
@@ -299,6 +306,197 @@ __device__ void prefix_products(LeafShared &S, int r, int lane, const Field &F)
     }
 }
 
+// Sum of up to 2^16 products of residues held exactly: one 64-bit word for
+// p <= 2^16 (products < 2^32), else a = a_hi 2^16 + a_lo in two words.
+template <bool SMALLP>
+struct LAcc {
+    uint64_t lo = 0, hi = 0;
+    __device__ __forceinline__ void add(uint32_t a, uint32_t b)
+    {
+        if (SMALLP) {
+            lo += (uint64_t)(a * b);
+        } else {
+            lo += (uint64_t)(a & 0xFFFFu) * b;
+            hi += (uint64_t)(a >> 16) * b;
+        }
+    }
+    __device__ __forceinline__ uint32_t value(const Field &F, uint32_t w16) const
+    {
+        if (SMALLP) return reduce64(lo, F);
+        return add_mod(reduce64(lo, F), mul_mod(reduce64(hi, F), w16, F), F.p);
+    }
+};
+
+constexpr int PB = 16;   // panel width of the generic path
+
+// Blocked LU without pivoting of the m x n block, staged in S.W.  Per panel of
+// PB pivot columns: (1) fraction-free elimination of the panel columns by the
+// warps that hold its rows (a lane per row), one named barrier per step and no
+// inverse on this path; (2) the panel's pivot values d_k, their prefix
+// products c_k and both inverses, in parallel, then normalisation to L21 and
+// U11; (3) U12 = L11^{-1} A12, one thread per column; (4) A22 -= L21 U12, each
+// element one delayed reduction.  Returns false, with A untouched, at the first
+// zero pivot (the rank profile is not generic).
+template <bool SMALLP>
+__device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, const Field &F,
+                           const Field32 &F32, LeafShared &S, int32_t *perm_p_out,
+                           int32_t *perm_q_out, int32_t *info_out, int info_len,
+                           volatile int32_t *host_info, int32_t seq)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t p = F.p;
+    const uint32_t w16 = (uint32_t)((1ull << 16) % p);
+    uint32_t *W = S.W;
+    for (int i = warp; i < m; i += NW)
+        for (int j = lane; j < n; j += 32) W[i * LD + j] = A[(int64_t)i * lda + j];
+    if (tid == 0) S.gfail = 0;
+    __syncthreads();
+    const int kmax = m < n ? m : n;
+    for (int j0 = 0; j0 < kmax; j0 += PB) {
+        const int b = kmax - j0 < PB ? kmax - j0 : PB;
+        const int R = m - j0;                        // panel rows
+        const int pw = (R + 31) / 32;                // warps holding them (<= 4)
+        // (1) fraction-free elimination of the panel columns
+        if (warp < pw) {
+            const int rel = warp * 32 + lane;        // this lane's panel row
+            const bool act = rel < R;
+            uint32_t w[PB];
+#pragma unroll
+            for (int c = 0; c < PB; ++c) w[c] = (act && c < b) ? W[(j0 + rel) * LD + j0 + c] : 0u;
+            // the step loop stays rolled (straight-line code executed once per
+            // panel would be fetch bound); the column loop is unrolled with
+            // predicated bodies, so w stays in registers
+            bool fail = false;
+#pragma unroll 1
+            for (int k = 0; k < b && !fail; ++k) {
+                if (warp == 0 && lane == k) {
+#pragma unroll
+                    for (int c = 0; c < PB; ++c) S.pbuf[k & 1][c] = w[c];
+                }
+                if (pw > 1) asm volatile("bar.sync 1, %0;" ::"r"(pw * 32) : "memory");
+                else __syncwarp();
+                // the pivot row in registers before any update uses it
+                uint32_t q[PB];
+#pragma unroll
+                for (int c = 0; c < PB; ++c) q[c] = S.pbuf[k & 1][c];
+                const uint32_t d = S.pbuf[k & 1][k];
+                fail = d == 0;
+                if (!fail && act && rel > k) {
+                    uint32_t fk = 0;
+#pragma unroll
+                    for (int c = 0; c < PB; ++c)
+                        if (c == k) fk = w[c];
+                    // computed for every column and kept by a select: the
+                    // independent updates overlap instead of running as one
+                    // branch after another
+#pragma unroll
+                    for (int c = 1; c < PB; ++c) {
+                        const uint32_t nv = ff_update<SMALLP>(d, w[c], fk, q[c], F, F32);
+                        w[c] = (c > k && c < b) ? nv : w[c];
+                    }
+                }
+            }
+            if (fail) {
+                if (tid == 0) S.gfail = 1;
+            } else {
+                // (2) row k (lane k of warp 0) holds d_k = w[k], untouched since
+                // step k.  One inversion serves the panel: with D = prod d_k,
+                // c_k = prod_{j<k} d_j and s_k = prod_{j>=k} d_j,
+                // 1/d_k = c_k s_{k+1} / D and 1/c_k = s_k / D.
+                if (warp == 0) {
+                    uint32_t dv = 1;
+#pragma unroll
+                    for (int c = 0; c < PB; ++c)
+                        if (c == lane && c < b) dv = w[c];
+                    uint32_t pre = dv, suf = dv;                        // inclusive scans
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+                        const uint32_t u = __shfl_down_sync(0xFFFFFFFFu, suf, o);
+                        if (lane >= o) pre = scale<SMALLP>(pre, v, F, F32);
+                        if (lane + o < 32) suf = scale<SMALLP>(suf, u, F, F32);
+                    }
+                    uint32_t ce = __shfl_up_sync(0xFFFFFFFFu, pre, 1);    // c_lane
+                    if (lane == 0) ce = 1;
+                    uint32_t se = __shfl_down_sync(0xFFFFFFFFu, suf, 1);  // s_{lane+1}
+                    if (lane == 31) se = 1;
+                    // D^(p-2) = 1/D (Fermat), square and multiply
+                    uint32_t iD = 1, base = __shfl_sync(0xFFFFFFFFu, pre, 31);
+                    for (uint32_t e = p - 2; e; e >>= 1) {
+                        if (e & 1u) iD = scale<SMALLP>(iD, base, F, F32);
+                        base = scale<SMALLP>(base, base, F, F32);
+                    }
+                    if (lane < b) {
+                        S.inv_d[lane] = scale<SMALLP>(scale<SMALLP>(ce, se, F, F32), iD, F, F32);
+                        S.inv_c[lane] = scale<SMALLP>(suf, iD, F, F32);
+                    }
+                }
+                if (pw > 1) asm volatile("bar.sync 1, %0;" ::"r"(pw * 32) : "memory");
+                else __syncwarp();
+                // L entries (c < rel) times 1/d_c; U entries of pivot rows (c >= rel)
+                // times 1/c_rel
+                if (act) {
+                    const uint32_t ic = rel < b ? S.inv_c[rel] : 0u;
+#pragma unroll
+                    for (int c = 0; c < PB; ++c)
+                        if (c < b) {
+                            const uint32_t sc = c < rel ? S.inv_d[c] : ic;
+                            W[(j0 + rel) * LD + j0 + c] = scale<SMALLP>(w[c], sc, F, F32);
+                        }
+                }
+            }
+        }
+        __syncthreads();
+        if (S.gfail) return false;
+        // (3) U12 = L11^{-1} A12 on the pivot rows, one thread per column
+        for (int c = j0 + b + tid; c < n; c += LT) {
+            uint32_t x[PB];
+#pragma unroll
+            for (int i = 0; i < PB; ++i) {
+                if (i < b) {
+                    LAcc<SMALLP> acc;
+#pragma unroll
+                    for (int k = 0; k < PB; ++k)
+                        if (k < i) acc.add(W[(j0 + i) * LD + j0 + k], x[k]);
+                    x[i] = sub_mod(W[(j0 + i) * LD + c], acc.value(F, w16), p);
+                    W[(j0 + i) * LD + c] = x[i];
+                }
+            }
+        }
+        __syncthreads();
+        // (4) A22 -= L21 U12
+        for (int i = j0 + b + warp; i < m; i += NW)
+            for (int c = j0 + b + lane; c < n; c += 32) {
+                LAcc<SMALLP> acc;
+#pragma unroll
+                for (int k = 0; k < PB; ++k)
+                    if (k < b) acc.add(W[i * LD + j0 + k], W[(j0 + k) * LD + c]);
+                W[i * LD + c] = sub_mod(W[i * LD + c], acc.value(F, w16), p);
+            }
+        __syncthreads();
+    }
+    // the packed block, P = Q = I, r = min(m, n)
+    for (int i = warp; i < m; i += NW)
+        for (int j = lane; j < n; j += 32) A[(int64_t)i * lda + j] = W[i * LD + j];
+    for (int i = tid; i < m; i += LT) perm_p_out[i] = i;
+    for (int j = tid; j < n; j += LT) perm_q_out[j] = j;
+    if (tid == 0) {
+        info_out[0] = kmax;
+        if (info_len > 2) {
+            info_out[1] = 1;
+            info_out[2] = 1;
+        }
+        if (host_info) {
+            host_info[1] = kmax;
+            host_info[2] = 1;
+            host_info[3] = 1;
+            __threadfence_system();
+            host_info[0] = seq;
+        }
+    }
+    return true;
+}
+
 // CPL column slots per lane (block width <= 32 CPL), RPW row slots per warp
 // (block height <= NW RPW): only slots that can hold data are compiled in.
 template <bool SMALLP, int CPL, int RPW>
@@ -313,6 +511,10 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = F.p;
     const Field32 F32{p, 0xFFFFFFFFu / p};
+    if (generic_lu<SMALLP>(A, m, n, lda, F, F32, S, perm_p_out, perm_q_out, info_out, info_len,
+                           host_info, seq))
+        return;
+    __syncthreads();   // the generic attempt is over: S belongs to the three phases now
 
     // this warp's rows warp + NW t and this lane's columns lane + 32 s, in registers
     uint32_t w[RPW][CPL];
@@ -360,11 +562,9 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
         if (tid == 0) S.key[(step + 1) % 3] = NOKEY;
         const int t0 = pi < warp ? 0 : (pi - warp) / NW + 1;   // first own row below pi
         uint32_t prow[CPL];
-        if (pi >= 0) {
 #pragma unroll
-            for (int s = 0; s < CPL; ++s)
-                if (s < ncl) prow[s] = S.cand[(step - 1) & 1][win][lane + 32 * s];
-        }
+        for (int s = 0; s < CPL; ++s)
+            prow[s] = (pi >= 0 && s < ncl) ? S.cand[(step - 1) & 1][win][lane + 32 * s] : 0u;
         const int spc = pc >> 5, lpc = pc & 31;
         bool offered = false;
 #pragma unroll
@@ -372,12 +572,14 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
             if (t < t0) continue;
             if (t >= tmax) break;
             if (pi >= 0) {
-                // d w - f q also covers f = 0 (then it scales by d): no branch
+                // d w - f q also covers f = 0 (then it scales by d); every slot is
+                // computed and kept by a select, so the updates overlap
                 const uint32_t f = __shfl_sync(0xFFFFFFFFu, pick<CPL>(w[t], spc), lpc);
 #pragma unroll
-                for (int s = 0; s < CPL; ++s)
-                    if (s < ncl && ((live >> s) & 1))
-                        w[t][s] = ff_update<SMALLP>(d, w[t][s], f, prow[s], F, F32);
+                for (int s = 0; s < CPL; ++s) {
+                    const uint32_t nv = ff_update<SMALLP>(d, w[t][s], f, prow[s], F, F32);
+                    w[t][s] = (s < ncl && ((live >> s) & 1)) ? nv : w[t][s];
+                }
             }
             if (!offered) {
                 int best = NOKEY;
@@ -534,8 +736,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
 #pragma unroll
                 for (int s = 0; s < CPL; ++s) {
                     const int j = lane + 32 * s;
-                    if (s < ncl && j > k && j < n)
-                        w[t][s] = ff_update<SMALLP>(dk, w[t][s], f, prow[s], F, F32);
+                    const uint32_t nv = ff_update<SMALLP>(dk, w[t][s], f, prow[s], F, F32);
+                    w[t][s] = (s < ncl && j > k && j < n) ? nv : w[t][s];
                 }
             }
             // the owner of row k + 1 publishes it for the next step

@@ -8,22 +8,26 @@
 //   p  > 2^16 : a = a_hi 2^16 + a_lo, a_lo b < 2^47 and a_hi b < 2^46, two
 //               64-bit accumulators hold 2^17 terms each (K is cut into
 //               chunks of 2^16 by the launcher).
-// 64 x 64 output tile per block, 256 threads, 4 x 4 outputs per thread,
-// 16-deep K slices staged in shared memory.
+// T x T output tile per block (T = 64, 32 or 16: the largest that still gives
+// every SM a block), 256 threads, (T/16)^2 outputs per thread, 16-deep K
+// slices staged in shared memory.
+#include <initializer_list>
+
 #include "common.cuh"
 
 namespace pluq {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 enum { MODE_SUB = 0, MODE_ASSIGN = 1, MODE_NEG_ASSIGN = 2, MODE_ADD = 3 };
 
-template <bool BIG>
+template <bool BIG, int T>
 __global__ void __launch_bounds__(NT) mm_simt_kernel(
     uint32_t *__restrict__ C, int64_t ldc, const uint32_t *__restrict__ A, int64_t lda,
     const uint32_t *__restrict__ B, int64_t ldb, int M, int N, int K, Field F, int mode,
     int64_t sA, int64_t sB, int64_t sC)
 {
+    constexpr int BM = T, BN = T, R = T / 16;   // R x R outputs per thread
     __shared__ uint32_t As[BK][BM + 4];
     __shared__ uint32_t Bs[BK][BN + 4];
     const int tid = threadIdx.x;
@@ -34,15 +38,15 @@ __global__ void __launch_bounds__(NT) mm_simt_kernel(
     B += b * sB;
     C += b * sC;
 
-    uint64_t acc_lo[4][4], acc_hi[4][4];
+    uint64_t acc_lo[R][R], acc_hi[R][R];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc_lo[i][j] = acc_hi[i][j] = 0;
+        for (int j = 0; j < R; ++j) acc_lo[i][j] = acc_hi[i][j] = 0;
 
     for (int k0 = 0; k0 < K; k0 += BK) {
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < R; ++s) {
             int r = tid / 16 + 16 * s, kk = tid % 16;
             int gr = row0 + r, gk = k0 + kk;
             As[kk][r] = (gr < M && gk < K) ? A[(int64_t)gr * lda + gk] : 0u;
@@ -54,15 +58,15 @@ __global__ void __launch_bounds__(NT) mm_simt_kernel(
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            uint32_t a[4], bv[4];
+            uint32_t a[R], bv[R];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < R; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < R; ++j) {
                     if (BIG) {
                         acc_lo[i][j] += (uint64_t)(a[i] & 0xFFFFu) * bv[j];
                         acc_hi[i][j] += (uint64_t)(a[i] >> 16) * bv[j];
@@ -77,11 +81,11 @@ __global__ void __launch_bounds__(NT) mm_simt_kernel(
     const uint32_t p = F.p;
     const uint32_t w16 = (uint32_t)((1ull << 16) % p);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
         int gr = row0 + ty + 16 * i;
         if (gr >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
             int gc = col0 + tx + 16 * j;
             if (gc >= N) continue;
             uint32_t t = reduce64(acc_lo[i][j], F);
@@ -116,18 +120,26 @@ pluq_status launch_mm_simt(Blk C, const uint32_t *A, int64_t lda, const uint32_t
             PLUQ_TRY(launch_zero(Blk{C.ptr + b * sC, C.ld}, M, N, st));
         return PLUQ_OK;
     }
-    dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM), (unsigned)batch);
+    // the largest tile that still gives every SM a block
+    int tile = 16;
+    for (int t : {64, 32})
+        if (ceil_div(M, t) * ceil_div(N, t) * batch >= 148) {
+            tile = t;
+            break;
+        }
+    dim3 grid((unsigned)ceil_div(N, tile), (unsigned)ceil_div(M, tile), (unsigned)batch);
     for (int64_t k0 = 0; k0 < K; k0 += kchunk) {
         int64_t kc = K - k0 < kchunk ? K - k0 : kchunk;
         int md = mode;
         if (k0 > 0) md = (mode == MM_ASSIGN) ? MODE_ADD : MODE_SUB;
         prof::start(prof::SIMT_MM, st);
-        if (big)
-            mm_simt_kernel<true><<<grid, NT, 0, st>>>(C.ptr, C.ld, A + k0, lda, B + k0 * ldb, ldb,
-                                                      (int)M, (int)N, (int)kc, F, md, sA, sB, sC);
-        else
-            mm_simt_kernel<false><<<grid, NT, 0, st>>>(C.ptr, C.ld, A + k0, lda, B + k0 * ldb, ldb,
-                                                       (int)M, (int)N, (int)kc, F, md, sA, sB, sC);
+#define PLUQ_SIMT_CASE(BIGP, T)                                                                   \
+    if (big == BIGP && tile == T)                                                                \
+        mm_simt_kernel<BIGP, T><<<grid, NT, 0, st>>>(C.ptr, C.ld, A + k0, lda, B + k0 * ldb, ldb, \
+                                                     (int)M, (int)N, (int)kc, F, md, sA, sB, sC);
+        PLUQ_SIMT_CASE(true, 64) PLUQ_SIMT_CASE(true, 32) PLUQ_SIMT_CASE(true, 16)
+        PLUQ_SIMT_CASE(false, 64) PLUQ_SIMT_CASE(false, 32) PLUQ_SIMT_CASE(false, 16)
+#undef PLUQ_SIMT_CASE
         PLUQ_TRY(last_launch());
         prof::stop(prof::SIMT_MM, st, 2.0 * (double)M * N * kc * batch);
     }

@@ -19,7 +19,6 @@
 namespace pluq {
 namespace {
 
-constexpr int TB = 32;
 
 // Sum of up to 2^17 products a_l * b_l (a, b < 2^31) held exactly in 64-bit
 // words.  p <= 2^16: one word (products < 2^32).  Otherwise a = a_hi 2^16 +
@@ -43,117 +42,6 @@ struct Acc {
     }
 };
 
-// Diagonal-block inverses, one 128-thread block per TB x TB diagonal block.
-// Thread (g, j) owns column j and the rows i = g, g + RG, ..., and keeps the
-// running sums of its entries in registers; X is produced row by row (one
-// barrier per row), each finished row feeding the sums of the rows after it.
-constexpr int BT = 128, RG = BT / TB, RPT = TB / RG;   // row groups, rows per thread
-
-// X_b = (diagonal block b of L)^-1, L unit lower:
-// X[i][j] = -sum_{j <= l < i} L[i][l] X[l][j] for i > j, X[j][j] = 1.
-template <bool SMALLP>
-__global__ void __launch_bounds__(BT) inv_lower_unit_base(const uint32_t *__restrict__ L,
-                                                          int64_t ldl, uint32_t *__restrict__ X,
-                                                          int64_t ldx, int r, Field F)
-{
-    __shared__ uint32_t Ls[TB][TB + 1];
-    __shared__ uint32_t Xs[TB][TB + 1];
-    const int o = blockIdx.x * TB;
-    const int sb = min(TB, r - o);
-    const int j = threadIdx.x % TB, g = threadIdx.x / TB;
-#pragma unroll 16
-    for (int e = threadIdx.x; e < TB * TB; e += BT) {
-        const int i = e / TB, c = e % TB;
-        Ls[i][c] = (i < sb && c < sb) ? L[(int64_t)(o + i) * ldl + o + c] : 0u;
-    }
-    Acc<SMALLP> acc[RPT];
-    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    __syncthreads();
-    for (int l = 0; l < sb; ++l) {
-        if (l % RG == g) {
-            uint32_t v;
-            if (l < j) v = 0;
-            else if (l == j) v = 1;
-            else {
-                uint32_t s = 0;
-#pragma unroll
-                for (int t = 0; t < RPT; ++t)
-                    if (g + RG * t == l) s = acc[t].value(F, w16);
-                v = s == 0 ? 0 : F.p - s;
-            }
-            Xs[l][j] = v;
-        }
-        __syncthreads();
-        const uint32_t xl = Xs[l][j];
-        if (xl != 0) {
-#pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                const int i = g + RG * t;
-                if (i > l) acc[t].add(Ls[i][l], xl);
-            }
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < sb * sb; e += BT) {
-        const int i = e / sb, c = e % sb;
-        X[(int64_t)(o + i) * ldx + o + c] = Xs[i][c];
-    }
-}
-
-// X_b = (diagonal block b of U)^-1, U upper with nonzero diagonal:
-// X[i][j] = U[i][i]^-1 (delta_ij - sum_{i < l <= j} U[i][l] X[l][j]), rows bottom-up.
-template <bool SMALLP>
-__global__ void __launch_bounds__(BT) inv_upper_base(const uint32_t *__restrict__ U, int64_t ldu,
-                                                     uint32_t *__restrict__ X, int64_t ldx, int r,
-                                                     Field F)
-{
-    __shared__ uint32_t Us[TB][TB + 1];
-    __shared__ uint32_t Xs[TB][TB + 1];
-    __shared__ uint32_t dinv[TB];
-    const int o = blockIdx.x * TB;
-    const int sb = min(TB, r - o);
-    const int j = threadIdx.x % TB, g = threadIdx.x / TB;
-#pragma unroll 16
-    for (int e = threadIdx.x; e < TB * TB; e += BT) {
-        const int i = e / TB, c = e % TB;
-        Us[i][c] = (i < sb && c < sb) ? U[(int64_t)(o + i) * ldu + o + c] : 0u;
-    }
-    __syncthreads();
-    if (threadIdx.x < sb) dinv[threadIdx.x] = inv_mod(Us[threadIdx.x][threadIdx.x], F.p);
-    Acc<SMALLP> acc[RPT];
-    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    __syncthreads();
-    for (int l = sb - 1; l >= 0; --l) {
-        if (l % RG == g) {
-            uint32_t v;
-            if (l > j) v = 0;
-            else {
-                uint32_t s = 0;                              // sum_{l < t <= j} U[l][t] X[t][j]
-#pragma unroll
-                for (int t = 0; t < RPT; ++t)
-                    if (g + RG * t == l) s = acc[t].value(F, w16);
-                uint32_t rhs = (l == j) ? 1u : 0u;
-                v = mul_mod(sub_mod(rhs, s, F.p), dinv[l], F);
-            }
-            Xs[l][j] = v;
-        }
-        __syncthreads();
-        const uint32_t xl = Xs[l][j];
-        if (xl != 0) {
-#pragma unroll
-            for (int t = 0; t < RPT; ++t) {
-                const int i = g + RG * t;
-                if (i < l) acc[t].add(Us[i][l], xl);
-            }
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < sb * sb; e += BT) {
-        const int i = e / sb, c = e % sb;
-        X[(int64_t)(o + i) * ldx + o + c] = Xs[i][c];
-    }
-}
-
 // Direct solves for narrow triangles (r <= WR): one warp per right-hand side
 // (a column of B for the left solve, a row of B for the right one), lane q
 // owning triangle rows / columns q, q + 32, ...  The unknowns are produced one
@@ -162,6 +50,7 @@ __global__ void __launch_bounds__(BT) inv_upper_base(const uint32_t *__restrict_
 // The owner's sum over the earlier terms is reduced one step ahead, so a step's
 // dependency chain is one shuffle, one modular product and two subtractions.
 constexpr int WR = 128, WT = 256, WPB = WT / 32;
+constexpr int TB = WR;   // diagonal blocks the inverses start from
 
 template <bool SMALLP>
 __device__ __forceinline__ uint32_t prod_mod(uint32_t a, uint32_t b, const Field &F,
@@ -184,21 +73,33 @@ __device__ __forceinline__ T slot_pick(const T (&v)[RPL], int s)
 // odd row stride of the staged triangle: a lane per row reads without conflicts
 __host__ __device__ __forceinline__ int tri_ld(int r) { return (r & 1) ? r + 2 : r + 1; }
 
-// B (r x N) <- L^{-1} B, L unit lower (diagonal not read).
-template <bool SMALLP, int RPL>
+// B (r x N) <- L^{-1} B, L unit lower (diagonal not read).  IDENT: blockIdx.y
+// picks the diagonal block of L at o = blockIdx.y * blk (size min(blk, r - o))
+// and B receives its inverse there (the right-hand side is the identity).
+template <bool SMALLP, int RPL, bool IDENT>
 __global__ void __launch_bounds__(WT) trsm_left_warp(const uint32_t *__restrict__ L, int64_t ldl,
                                                       uint32_t *__restrict__ B, int64_t ldb, int r,
-                                                      int64_t N, Field F)
+                                                      int64_t N, Field F, int blk)
 {
     extern __shared__ uint32_t Ls[];
+    if (IDENT) {
+        const int64_t o = (int64_t)blockIdx.y * blk;
+        L += o * (ldl + 1);
+        B += o * (ldb + 1);
+        r = min(blk, (int)(r - o));
+        N = r;
+    }
     const int ld = tri_ld(r);
-    for (int e = threadIdx.x; e < r * r; e += WT) {
-        const int i = e / r, c = e % r;
-        if (c < i) Ls[i * ld + c] = L[(int64_t)i * ldl + c];
+    {
+        const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        for (int i = w; i < r; i += nw)
+#pragma unroll 4
+            for (int c = l; c < i; c += 32) Ls[i * ld + c] = L[(int64_t)i * ldl + c];
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t j = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *xs = Ls + r * ld + warp * WR;            // this warp's unknowns
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (j >= N) return;
     const Field32 F32{F.p, 0xFFFFFFFFu / F.p};
     const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
@@ -207,9 +108,11 @@ __global__ void __launch_bounds__(WT) trsm_left_warp(const uint32_t *__restrict_
 #pragma unroll
     for (int t = 0; t < RPL; ++t) {
         const int row = lane + 32 * t;
-        b[t] = row < r ? B[(int64_t)row * ldb + j] : 0u;
+        if (IDENT) b[t] = row == j ? 1u : 0u;
+        else b[t] = row < r ? B[(int64_t)row * ldb + j] : 0u;
     }
     uint32_t x = __shfl_sync(0xFFFFFFFFu, b[0], 0);   // x_0 = b_0
+    if (lane == 0) xs[0] = x;
     uint32_t vnext = 0;                               // owner's sum for row i + 1, terms < i
     for (int i = 0; i + 1 < r; ++i) {
         const int nr = i + 1, nl = nr & 31, ns = nr >> 5;
@@ -220,36 +123,48 @@ __global__ void __launch_bounds__(WT) trsm_left_warp(const uint32_t *__restrict_
         for (int t = 0; t < RPL; ++t) {
             const int row = lane + 32 * t;
             if (row > nr && row < r) acc[t].add(Ls[row * ld + i], x);
-            if (t == ns && lane == nl) b[t] = xn;
         }
         x = __shfl_sync(0xFFFFFFFFu, xn, nl);
+        if (lane == 0) xs[nr] = x;
         vnext = slot_pick<RPL>(acc, (i + 2) >> 5).value(F, w16);
     }
+    __syncwarp();
 #pragma unroll
     for (int t = 0; t < RPL; ++t) {
         const int row = lane + 32 * t;
-        if (row < r) B[(int64_t)row * ldb + j] = b[t];
+        if (row < r) B[(int64_t)row * ldb + j] = xs[row];
     }
 }
 
-// B (M x r) <- B U^{-1}, U upper with nonzero diagonal.
-template <bool SMALLP, int RPL>
+// B (M x r) <- B U^{-1}, U upper with nonzero diagonal.  IDENT: as for the
+// left solve, B receives the inverse of the diagonal block blockIdx.y of U.
+template <bool SMALLP, int RPL, bool IDENT>
 __global__ void __launch_bounds__(WT) trsm_right_warp(const uint32_t *__restrict__ U, int64_t ldu,
                                                        uint32_t *__restrict__ B, int64_t ldb,
-                                                       int64_t M, int r, Field F)
+                                                       int64_t M, int r, Field F, int blk)
 {
     extern __shared__ uint32_t Us[];
+    if (IDENT) {
+        const int64_t o = (int64_t)blockIdx.y * blk;
+        U += o * (ldu + 1);
+        B += o * (ldb + 1);
+        r = min(blk, (int)(r - o));
+        M = r;
+    }
     const int ld = tri_ld(r);
     uint32_t *dinv = Us + r * ld;
-    for (int e = threadIdx.x; e < r * r; e += WT) {
-        const int i = e / r, c = e % r;
-        if (c >= i) Us[i * ld + c] = U[(int64_t)i * ldu + c];
+    {
+        const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        for (int i = w; i < r; i += nw)
+#pragma unroll 4
+            for (int c = i + l; c < r; c += 32) Us[i * ld + c] = U[(int64_t)i * ldu + c];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < r; t += WT) dinv[t] = inv_mod(Us[t * ld + t], F.p);
+    for (int t = threadIdx.x; t < r; t += blockDim.x) dinv[t] = inv_mod(Us[t * ld + t], F.p);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *xs = dinv + WR + warp * WR;              // this warp's unknowns
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (i >= M) return;
     const Field32 F32{F.p, 0xFFFFFFFFu / F.p};
     const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
@@ -258,10 +173,11 @@ __global__ void __launch_bounds__(WT) trsm_right_warp(const uint32_t *__restrict
 #pragma unroll
     for (int t = 0; t < RPL; ++t) {
         const int c = lane + 32 * t;
-        b[t] = c < r ? B[i * ldb + c] : 0u;
+        if (IDENT) b[t] = c == i ? 1u : 0u;
+        else b[t] = c < r ? B[i * ldb + c] : 0u;
     }
     uint32_t x = prod_mod<SMALLP>(__shfl_sync(0xFFFFFFFFu, b[0], 0), dinv[0], F, F32);
-    if (lane == 0) b[0] = x;
+    if (lane == 0) xs[0] = x;
     uint32_t vnext = 0;
     for (int l = 0; l + 1 < r; ++l) {
         const int nc = l + 1, nl = nc & 31, ns = nc >> 5;
@@ -274,53 +190,72 @@ __global__ void __launch_bounds__(WT) trsm_right_warp(const uint32_t *__restrict
         for (int t = 0; t < RPL; ++t) {
             const int c = lane + 32 * t;
             if (c > nc && c < r) acc[t].add(Us[l * ld + c], x);
-            if (t == ns && lane == nl) b[t] = xn;
         }
         x = __shfl_sync(0xFFFFFFFFu, xn, nl);
+        if (lane == 0) xs[nc] = x;
         vnext = slot_pick<RPL>(acc, (l + 2) >> 5).value(F, w16);
     }
+    __syncwarp();
 #pragma unroll
     for (int t = 0; t < RPL; ++t) {
         const int c = lane + 32 * t;
-        if (c < r) B[i * ldb + c] = b[t];
+        if (c < r) B[i * ldb + c] = xs[c];
     }
 }
 
+// left: B (r x other) <- T^{-1} B; otherwise B (other x r) <- B T^{-1}.  With
+// `blocks` > 0 the diagonal blocks of size min(WR, .) of T are inverted into B
+// instead (other is ignored).
 template <bool SMALLP, int RPL>
 pluq_status launch_trsm_warp(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_t other,
-                             int r, Field F, cudaStream_t st)
+                             int r, Field F, int64_t blocks, cudaStream_t st)
 {
-    const size_t smem = ((size_t)r * tri_ld(r) + (left ? 0 : r)) * sizeof(uint32_t);
-    const unsigned grid = (unsigned)ceil_div(other, WPB);
-    if (left) {
-        static const bool attr = cudaFuncSetAttribute(trsm_left_warp<SMALLP, RPL>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)(WR * tri_ld(WR) * 4)) == cudaSuccess;
-        if (!attr) return PLUQ_ECUDA;
-        trsm_left_warp<SMALLP, RPL><<<grid, WT, smem, st>>>(T, ldt, B.ptr, B.ld, r, other, F);
-    } else {
-        static const bool attr = cudaFuncSetAttribute(trsm_right_warp<SMALLP, RPL>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)((WR * tri_ld(WR) + WR) * 4)) == cudaSuccess;
-        if (!attr) return PLUQ_ECUDA;
-        trsm_right_warp<SMALLP, RPL><<<grid, WT, smem, st>>>(T, ldt, B.ptr, B.ld, other, r, F);
+    const int rr = blocks > 0 ? (r < WR ? r : WR) : r;
+    const int64_t rhs = blocks > 0 ? rr : other;
+    const int64_t nb = blocks > 0 ? blocks : 1;
+    const int wpb = WPB;
+    const size_t smem = ((size_t)rr * tri_ld(rr) + (left ? 0 : WR) + (size_t)wpb * WR) * sizeof(uint32_t);
+    const dim3 grid((unsigned)ceil_div(rhs, wpb), (unsigned)nb);
+    const int nt = 32 * wpb;
+    const int full = (WR * tri_ld(WR) + WPB * WR) * 4, fullr = (WR * tri_ld(WR) + WR + WPB * WR) * 4;
+#define PLUQ_TRSM_ATTR(K, BYTES)                                                                   \
+    {                                                                                             \
+        static const bool attr =                                                                  \
+            cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES) ==        \
+            cudaSuccess;                                                                          \
+        if (!attr) return PLUQ_ECUDA;                                                             \
     }
+    if (left && blocks > 0) {
+        PLUQ_TRSM_ATTR((trsm_left_warp<SMALLP, RPL, true>), full)
+        trsm_left_warp<SMALLP, RPL, true><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, r, 0, F, WR);
+    } else if (left) {
+        PLUQ_TRSM_ATTR((trsm_left_warp<SMALLP, RPL, false>), full)
+        trsm_left_warp<SMALLP, RPL, false><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, r, other, F, 0);
+    } else if (blocks > 0) {
+        PLUQ_TRSM_ATTR((trsm_right_warp<SMALLP, RPL, true>), fullr)
+        trsm_right_warp<SMALLP, RPL, true><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, 0, r, F, WR);
+    } else {
+        PLUQ_TRSM_ATTR((trsm_right_warp<SMALLP, RPL, false>), fullr)
+        trsm_right_warp<SMALLP, RPL, false><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, other, r, F, 0);
+    }
+#undef PLUQ_TRSM_ATTR
     return last_launch();
 }
 
 pluq_status trsm_direct(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_t other, int r,
-                        Field F, cudaStream_t st)
+                        Field F, int64_t blocks, cudaStream_t st)
 {
     const bool sp = F.p <= 65536u;
-    const int rpl = r <= 32 ? 1 : r <= 64 ? 2 : 4;
+    const int rb = blocks > 0 ? (r < WR ? r : WR) : r;
+    const int rpl = rb <= 32 ? 1 : rb <= 64 ? 2 : 4;
     if (sp) {
-        if (rpl == 1) return launch_trsm_warp<true, 1>(left, T, ldt, B, other, r, F, st);
-        if (rpl == 2) return launch_trsm_warp<true, 2>(left, T, ldt, B, other, r, F, st);
-        return launch_trsm_warp<true, 4>(left, T, ldt, B, other, r, F, st);
+        if (rpl == 1) return launch_trsm_warp<true, 1>(left, T, ldt, B, other, r, F, blocks, st);
+        if (rpl == 2) return launch_trsm_warp<true, 2>(left, T, ldt, B, other, r, F, blocks, st);
+        return launch_trsm_warp<true, 4>(left, T, ldt, B, other, r, F, blocks, st);
     }
-    if (rpl == 1) return launch_trsm_warp<false, 1>(left, T, ldt, B, other, r, F, st);
-    if (rpl == 2) return launch_trsm_warp<false, 2>(left, T, ldt, B, other, r, F, st);
-    return launch_trsm_warp<false, 4>(left, T, ldt, B, other, r, F, st);
+    if (rpl == 1) return launch_trsm_warp<false, 1>(left, T, ldt, B, other, r, F, blocks, st);
+    if (rpl == 2) return launch_trsm_warp<false, 2>(left, T, ldt, B, other, r, F, blocks, st);
+    return launch_trsm_warp<false, 4>(left, T, ldt, B, other, r, F, blocks, st);
 }
 
 }  // namespace
@@ -331,11 +266,7 @@ pluq_status tri_inv_lower_unit(const uint32_t *L, int64_t ldl, Blk X, int64_t r,
     if (r <= 0) return PLUQ_OK;
     PLUQ_TRY(launch_zero(X, r, r, st));
     prof::start(prof::TRI, st);
-    if (F.p <= 65536u)
-        inv_lower_unit_base<true><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(L, ldl, X.ptr, X.ld, (int)r, F);
-    else
-        inv_lower_unit_base<false><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(L, ldl, X.ptr, X.ld, (int)r, F);
-    PLUQ_TRY(last_launch());
+    PLUQ_TRY(trsm_direct(true, L, ldl, X, 0, (int)r, F, ceil_div(r, TB), st));
     prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;
     size_t mark = ar.off;
@@ -372,11 +303,7 @@ pluq_status tri_inv_upper(const uint32_t *U, int64_t ldu, Blk X, int64_t r, Fiel
     if (r <= 0) return PLUQ_OK;
     PLUQ_TRY(launch_zero(X, r, r, st));
     prof::start(prof::TRI, st);
-    if (F.p <= 65536u)
-        inv_upper_base<true><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(U, ldu, X.ptr, X.ld, (int)r, F);
-    else
-        inv_upper_base<false><<<(unsigned)ceil_div(r, TB), BT, 0, st>>>(U, ldu, X.ptr, X.ld, (int)r, F);
-    PLUQ_TRY(last_launch());
+    PLUQ_TRY(trsm_direct(false, U, ldu, X, 0, (int)r, F, ceil_div(r, TB), st));
     prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;
     size_t mark = ar.off;
@@ -432,7 +359,7 @@ pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t 
     if (r <= 0 || N <= 0) return PLUQ_OK;
     if (r <= WR) {
         prof::start(prof::TRI, st);
-        pluq_status s = trsm_direct(true, L, ldl, B, N, (int)r, F, st);
+        pluq_status s = trsm_direct(true, L, ldl, B, N, (int)r, F, 0, st);
         prof::stop(prof::TRI, st, (double)r * r * N / 2.0);
         return s;
     }
@@ -459,7 +386,7 @@ pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, i
     if (r <= 0 || M <= 0) return PLUQ_OK;
     if (r <= WR) {
         prof::start(prof::TRI, st);
-        pluq_status s = trsm_direct(false, U, ldu, B, M, (int)r, F, st);
+        pluq_status s = trsm_direct(false, U, ldu, B, M, (int)r, F, 0, st);
         prof::stop(prof::TRI, st, (double)r * r * M / 2.0);
         return s;
     }

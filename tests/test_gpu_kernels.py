@@ -58,6 +58,39 @@ def test_leaf_matches_oracle(p):
         assert np.array_equal(host(d), LU0), (m, n)
 
 
+def _lu_product(g, m, n, p, zero_at):
+    """L0 U0 mod p with L0 unit lower (m x m) and U0 upper (m x n) whose
+    diagonal is nonzero except at `zero_at`: the leading minors are nonzero
+    exactly up to order zero_at."""
+    L0 = np.tril(g.integers(0, p, (m, m)), -1) + np.eye(m, dtype=np.int64)
+    U0 = np.triu(g.integers(0, p, (m, n)), 1)
+    for k in range(min(m, n)):
+        U0[k, k] = 0 if k == zero_at else int(g.integers(1, p))
+    return (L0.astype(object).dot(U0.astype(object)) % p).astype(np.uint32)
+
+
+@pytest.mark.parametrize("p", PRIMES)
+def test_leaf_generic_rank_profile_and_late_fallback(p):
+    """Blocks with all leading minors nonzero (the blocked path without
+    pivoting) and blocks whose first zero minor comes only after one or more
+    panels (the hand-over to the general path after work was done)."""
+    g = np.random.Generator(np.random.PCG64(p + 77))
+    cases = []
+    for (m, n) in [(64, 64), (128, 128), (100, 37), (37, 100), (17, 1), (1, 17), (128, 50),
+                   (33, 33)]:
+        k = min(m, n)
+        cases += [(m, n, None), (m, n, k - 1), (m, n, k // 2), (m, n, 0)]
+    for (m, n, z) in cases:
+        A = _lu_product(g, m, n, p, -1 if z is None else z)
+        LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+        d = dev(A)
+        pp, pq, r = pluq.pluq_leaf(d, p)
+        assert r == r0, (m, n, z)
+        assert np.array_equal(pp.cpu().numpy(), pp0), (m, n, z)
+        assert np.array_equal(pq.cpu().numpy(), pq0), (m, n, z)
+        assert np.array_equal(host(d), LU0), (m, n, z)
+
+
 def test_leaf_exhaustive_gf2_4x4():
     As = brute.all_matrices(4, 4, 2)[::5]
     for A in As:
