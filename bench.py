@@ -190,6 +190,19 @@ def committed_traffic(kernel_class: str, workload: str):
     return ent.get("dram_bytes_per_launch")
 
 
+def alu_field_peak():
+    """Field operations per second the integer ALUs could issue: every SM lane
+    issuing one instruction per cycle at the maximum SM clock, five lane
+    instructions per field operation (a multiply-add mod p is a product, a
+    Barrett quotient, a product by p and two min-folds)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = json.load(f).get("sm_max_mhz", 2070.0)
+    except (OSError, ValueError):
+        mhz = 2070.0
+    return 152 * 128 * mhz * 1e6 / 5 / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -263,21 +276,26 @@ def run_ours(args):
     barrier()
     launches = pluq.pluq_launch_count() - launches0
     clk = clocks.stop()
-    # the same steps again with the roofline kernel's launches bracketed by
-    # CUDA events on their stream (kept out of the region `value` comes from)
-    roof_class = "tensor_mm" if args.mm == "tensor" else "simt_mm"
-    pluq.pluq_profile_enable([roof_class])
-    for _ in range(args.steps):
-        step(args.mm)
-    torch.cuda.synchronize()
-    pluq.pluq_profile_enable(False)
-    roof_stats = pluq.pluq_profile_read(roof_class)
-    # every class, one more pass, for the breakdown
+    # every kernel class bracketed by CUDA events, one more pass, for the
+    # breakdown and to find the dominant class (kept out of the timed region)
     pluq.pluq_profile_enable(True)
     for _ in range(max(1, args.steps // 2)):
         step(args.mm)
     torch.cuda.synchronize()
     pluq.pluq_profile_enable(False)
+    breakdown = {name: pluq.pluq_profile_read(name) for name in pluq.PROFILE_CLASSES}
+    dominant = max(breakdown, key=lambda k: breakdown[k][1])
+    # the same steps again with only the dominant class's launches bracketed by
+    # CUDA events on their stream, then only the product's
+    mm_class = "tensor_mm" if args.mm == "tensor" else "simt_mm"
+    live = {}
+    for cls in dict.fromkeys([dominant, mm_class]):
+        pluq.pluq_profile_enable([cls])
+        for _ in range(args.steps):
+            step(args.mm)
+        torch.cuda.synchronize()
+        pluq.pluq_profile_enable(False)
+        live[cls] = pluq.pluq_profile_read(cls)
     times = [a.elapsed_time(b) for a, b, _ in evs]
     r = evs[-1][2]
     total_ms = sum(times)
@@ -289,12 +307,9 @@ def run_ours(args):
     value = world * args.steps * work / (total_ms / 1e3) / 1e9
 
     # per-class device time (event-bracketed launches) for the breakdown
-    classes = {}
-    for name in pluq.PROFILE_CLASSES:
-        nl, ms, w = pluq.pluq_profile_read(name)
-        classes[name] = {"launches": nl, "ms": ms, "work": w}
-    dominant = max(classes, key=lambda k: classes[k]["ms"])
+    classes = {name: {"launches": v[0], "ms": v[1], "work": v[2]} for name, v in breakdown.items()}
     hbm_peak, bf16_peak, peak_src = measured_peaks()
+    alu_peak = alu_field_peak()
 
     def roofline_for(name, stats=None):
         c = classes[name] if stats is None else {"launches": stats[0], "ms": stats[1],
@@ -306,23 +321,34 @@ def run_ours(args):
         if name in ("tensor_mm",):
             bound, unit, peak = "tensor", "TFLOP/s", bf16_peak
             achieved = per_launch_work / per_launch_s / 1e12
-        elif name in ("move", "split", "leaf"):
+            src = f"{peak_src} bf16 burst (MEASURED_PEAKS.json)"
+        elif name in ("move", "split"):
             bound, unit, peak = "hbm", "GB/s", hbm_peak
             achieved = per_launch_work / per_launch_s / 1e9
+            src = f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)"
         else:
-            bound, unit, peak = "alu", "Gop/s", None
+            # modular field operations on the integer ALUs (leaf, TRSM, CUDA-core product)
+            bound, unit, peak = "alu", "Gfop/s", alu_peak
             achieved = per_launch_work / per_launch_s / 1e9
+            src = ("derived: 152 SMs x 128 lanes x max SM clock, at 5 lane instructions "
+                   "per field operation")
         return {"kernel_class": name, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": (achieved / peak) if peak else None,
                 "traffic": committed_traffic(name, args.workload),
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json burst)" if peak else None,
+                "peak_source": src,
                 "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6,
                 "share_of_step": c["ms"] / max(sum(times), 1e-9)}
 
-    roof = roofline_for(roof_class, roof_stats)
-    roof["dominant_class_in_breakdown"] = dominant
-    roof["measured"] = (f"CUDA events around each {roof_class} launch on its stream over "
-                        f"{args.steps} instrumented steps that follow the timed ones")
+    def measured_note(cls):
+        return (f"CUDA events around each {cls} launch on its stream over {args.steps} "
+                f"instrumented steps that follow the timed ones")
+
+    roof = roofline_for(dominant, live[dominant])
+    roof["dominant"] = True
+    roof["measured"] = measured_note(dominant)
+    roof_mm = roofline_for(mm_class, live[mm_class])
+    if roof_mm:
+        roof_mm["measured"] = measured_note(mm_class)
 
     # ---------------- plain CUDA-core form on the same workload (context)
     simt_value = None
@@ -415,6 +441,7 @@ def run_ours(args):
                                   "source": "autotune over leaf {32,64,128} x small-product "
                                             "threshold {2^24,2^25,2^27}"}},
             "roofline": roof,
+            "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,
             "kernel_classes": classes,
             "plain_cuda_core_value": simt_value,

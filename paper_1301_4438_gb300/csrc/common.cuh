@@ -267,10 +267,13 @@ pluq_status launch_extract(const uint32_t *LU, int64_t lda, int64_t rows, int64_
 constexpr int LEAF_MAX = 128;
 // info[0] = r, info[1] = (P is the identity), info[2] = (Q is the identity);
 // when host_info is given (mapped pinned memory) the same three words go to
-// host_info[1..3] and then seq to host_info[0].
+// host_info[1..3] and then seq to host_info[0].  try_generic: attempt the
+// blocked path for a generic rank profile first (worth it unless the block
+// lies in a rank-deficient region, where it would fail at once).
 pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
                         int32_t *perm_p, int32_t *perm_q, int32_t *info, int info_len,
-                        cudaStream_t st, volatile int32_t *host_info = nullptr, int32_t seq = 0);
+                        cudaStream_t st, volatile int32_t *host_info = nullptr, int32_t seq = 0,
+                        bool try_generic = true);
 
 // Process-wide tuning (pluq_set_tuning): leaf size of the recursion, and the
 // number of multiply-adds below which a product goes to the CUDA-core kernel

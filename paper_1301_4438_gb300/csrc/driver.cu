@@ -34,7 +34,7 @@ pluq_status launch_any_nonzero(const uint32_t *A, int64_t lda, int64_t m, int64_
                                volatile int32_t *host, int32_t seq, cudaStream_t st);
 
 std::atomic<int64_t> g_tune_small_mm{1ll << 25};
-std::atomic<int64_t> g_tune_leaf{64};
+std::atomic<int64_t> g_tune_leaf{128};
 
 namespace {
 // byte ranges [lo, hi) spanned by a batch of strided blocks
@@ -145,7 +145,7 @@ struct Ctx {
     size_t vtop, vcap;
     int32_t *d_rank;      // device words: range check flag, leaf info
     HostWords *hw;
-    int64_t leaf = 64;    // blocks with both sides <= leaf go to the leaf kernel
+    int64_t leaf = 128;   // blocks with both sides <= leaf go to the leaf kernel
     int64_t leaves = 0;
     int64_t zero_checks = 0;
 };
@@ -163,7 +163,7 @@ int64_t initial_leaf()
         long v = strtol(e, nullptr, 10);
         if (v >= 16 && v <= LEAF_MAX) return v;
     }
-    return 64;
+    return 128;
 }
 
 // result of a (sub)decomposition: rank, and whether P / Q are identities
@@ -210,13 +210,14 @@ bool in_order(const int64_t (*seg)[2], int count)
 // factorisation; pp / pq hold P / Q unless out.pid / out.qid say they are the
 // identity (then the vectors are not written).
 pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t *pp,
-                int32_t *pq, Res &out, int depth)
+                int32_t *pq, Res &out, int depth, bool eager)
 {
     out = Res{};
     if (m == 0 || n == 0) return PLUQ_OK;
     if (m <= c.leaf && n <= c.leaf) {
         const int32_t seq = ++c.hw->seq;
-        PLUQ_TRY(launch_leaf(A, m, n, lda, c.F, pp, pq, c.d_rank + 4, 3, c.st, c.hw->d, seq));
+        PLUQ_TRY(launch_leaf(A, m, n, lda, c.F, pp, pq, c.d_rank + 4, 3, c.st, c.hw->d, seq,
+                             !eager));
         PLUQ_TRY(wait_words(c.hw, seq, c.st));
         const int32_t r = c.hw->h[1];
         ++c.leaves;
@@ -228,12 +229,14 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     }
     // A block's rank is the number of ones of R inside it, so deep in the
     // recursion of a rank-deficient matrix most blocks are exactly zero: one
-    // pass over the block prunes the whole subtree (r = 0, P = Q = I).  The
-    // answer is read lazily: the descent into A1 goes ahead meanwhile and its
-    // first leaf (a synchronisation anyway) brings the answer along.  If the
-    // block is zero, so is A1, whose decomposition then changed nothing and
-    // reported r1 = 0 with identity permutations.
-    const bool lazy = depth < ZDEPTH;
+    // pass over the block prunes the whole subtree (r = 0, P = Q = I).  Below a
+    // node whose A1 turned out rank deficient the answer is awaited at once;
+    // elsewhere (full-rank regions, where blocks are rarely zero) it is read
+    // lazily: the descent into A1 goes ahead meanwhile and its first leaf (a
+    // synchronisation anyway) brings the answer along.  If the block is zero,
+    // so is A1, whose decomposition then changed nothing and reported r1 = 0
+    // with identity permutations.
+    const bool lazy = !eager && depth < ZDEPTH;
     const int32_t zseq = ++c.hw->seq;
     const int zat = ZBASE + 2 * depth;
     ++c.zero_checks;
@@ -255,7 +258,7 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
 
     // A1 = P1 [L1;M1][U1 V1] Q1
     Res s1;
-    PLUQ_TRY(rec(c, A, k, h, lda, p1, q1, s1, depth + 1));
+    PLUQ_TRY(rec(c, A, k, h, lda, p1, q1, s1, depth + 1, eager));
     if (lazy) {
         PLUQ_TRY(wait_words(c.hw, zseq, c.st, zat));
         if (c.hw->h[zat + 1] == 0) {
@@ -265,6 +268,7 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
         }
     }
     const int64_t r1 = s1.r;
+    const bool deficient = r1 < (k < h ? k : h);
     // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
     PLUQ_TRY(permute_block(c, at(0, h), lda, k, n - h, vec(p1, s1.pid), nullptr));
     PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, h, nullptr, vec(q1, s1.qid)));
@@ -278,8 +282,8 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
                        r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
     Res s2, s3;
-    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1));
-    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1));
+    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1, deficient));
+    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient));
     const int64_t r2 = s2.r, r3 = s3.r;
     int32_t *P2 = vec(p2, s2.pid), *Q2 = vec(q2, s2.qid), *P3 = vec(p3, s3.pid), *Q3 = vec(q3, s3.qid);
     // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
@@ -306,7 +310,8 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
                        lda, m - k - r3, n - h - r2, r3, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     // R = P4 [L4;M4][U4 V4] Q4
     Res s4;
-    PLUQ_TRY(rec(c, at(k + r3, h + r2), m - k - r3, n - h - r2, lda, p4, q4, s4, depth + 1));
+    PLUQ_TRY(rec(c, at(k + r3, h + r2), m - k - r3, n - h - r2, lda, p4, q4, s4, depth + 1,
+                 deficient));
     const int64_t r4 = s4.r;
     int32_t *P4 = vec(p4, s4.pid), *Q4 = vec(q4, s4.qid);
     // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T
@@ -460,7 +465,7 @@ pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p
     if (flag != 0) return PLUQ_ERANGE;
 
     Res res;
-    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res, 0));
+    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res, 0, false));
     if (res.pid) PLUQ_TRY(launch_iota(d_perm_p, m, st));
     if (res.qid) PLUQ_TRY(launch_iota(d_perm_q, n, st));
     PLUQ_CUDA_TRY(cudaStreamSynchronize(st));

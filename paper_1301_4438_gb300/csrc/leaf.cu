@@ -504,15 +504,15 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
                                                   int64_t lda, Field F, int32_t *perm_p_out,
                                                   int32_t *perm_q_out, int32_t *info_out,
                                                   int info_len, volatile int32_t *host_info,
-                                                  int32_t seq)
+                                                  int32_t seq, int try_generic)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = F.p;
     const Field32 F32{p, 0xFFFFFFFFu / p};
-    if (generic_lu<SMALLP>(A, m, n, lda, F, F32, S, perm_p_out, perm_q_out, info_out, info_len,
-                           host_info, seq))
+    if (try_generic && generic_lu<SMALLP>(A, m, n, lda, F, F32, S, perm_p_out, perm_q_out,
+                                          info_out, info_len, host_info, seq))
         return;
     __syncthreads();   // the generic attempt is over: S belongs to the three phases now
 
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
 
 pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F, int32_t *perm_p,
                         int32_t *perm_q, int32_t *info, int info_len, cudaStream_t st,
-                        volatile int32_t *host_info, int32_t seq)
+                        volatile int32_t *host_info, int32_t seq, bool try_generic)
 {
     if (m < 0 || n < 0 || m > LM || n > LM) return PLUQ_EINVAL;
     if (m == 0 || n == 0) {
@@ -835,7 +835,8 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
                                                       (int)smem) == cudaSuccess;                 \
         if (!attr) return PLUQ_ECUDA;                                                            \
         leaf_kernel<SP, C, R><<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q,    \
-                                                   info, info_len, host_info, seq);              \
+                                                   info, info_len, host_info, seq,               \
+                                                   try_generic ? 1 : 0);                         \
     }
     PLUQ_LEAF_CASE(true, 1, 2) PLUQ_LEAF_CASE(true, 1, 4) PLUQ_LEAF_CASE(true, 1, 8)
     PLUQ_LEAF_CASE(true, 2, 2) PLUQ_LEAF_CASE(true, 2, 4) PLUQ_LEAF_CASE(true, 2, 8)
@@ -846,7 +847,10 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
 #undef PLUQ_LEAF_CASE
     (void)ls;
     pluq_status s = last_launch();
-    prof::stop(prof::LEAF, st, (double)m * n * 8.0);
+    // algorithmic work: the field operations of eliminating the block at full
+    // rank, 2 m n k - (m + n) k^2 + 2/3 k^3 with k = min(m, n)
+    const double k = (double)(m < n ? m : n);
+    prof::stop(prof::LEAF, st, 2.0 * m * n * k - (double)(m + n) * k * k + 2.0 / 3.0 * k * k * k);
     return s;
 }
 

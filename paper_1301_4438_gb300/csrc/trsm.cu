@@ -267,7 +267,7 @@ pluq_status tri_inv_lower_unit(const uint32_t *L, int64_t ldl, Blk X, int64_t r,
     PLUQ_TRY(launch_zero(X, r, r, st));
     prof::start(prof::TRI, st);
     PLUQ_TRY(trsm_direct(true, L, ldl, X, 0, (int)r, F, ceil_div(r, TB), st));
-    prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
+    prof::stop(prof::TRI, st, 2.0 * (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;
     size_t mark = ar.off;
     uint32_t *T = (uint32_t *)ar.take((size_t)r * r * sizeof(uint32_t));
@@ -304,7 +304,7 @@ pluq_status tri_inv_upper(const uint32_t *U, int64_t ldu, Blk X, int64_t r, Fiel
     PLUQ_TRY(launch_zero(X, r, r, st));
     prof::start(prof::TRI, st);
     PLUQ_TRY(trsm_direct(false, U, ldu, X, 0, (int)r, F, ceil_div(r, TB), st));
-    prof::stop(prof::TRI, st, (double)r * TB * TB / 3.0);
+    prof::stop(prof::TRI, st, 2.0 * (double)r * TB * TB / 3.0);
     if (r <= TB) return PLUQ_OK;
     size_t mark = ar.off;
     uint32_t *T = (uint32_t *)ar.take((size_t)r * r * sizeof(uint32_t));
@@ -360,7 +360,7 @@ pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t 
     if (r <= WR) {
         prof::start(prof::TRI, st);
         pluq_status s = trsm_direct(true, L, ldl, B, N, (int)r, F, 0, st);
-        prof::stop(prof::TRI, st, (double)r * r * N / 2.0);
+        prof::stop(prof::TRI, st, (double)r * r * N);   // field operations
         return s;
     }
     size_t mark = ar.off;
@@ -387,7 +387,7 @@ pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, i
     if (r <= WR) {
         prof::start(prof::TRI, st);
         pluq_status s = trsm_direct(false, U, ldu, B, M, (int)r, F, 0, st);
-        prof::stop(prof::TRI, st, (double)r * r * M / 2.0);
+        prof::stop(prof::TRI, st, (double)r * r * M);   // field operations
         return s;
     }
     size_t mark = ar.off;
