@@ -145,6 +145,36 @@ pluq_status pluq_extract_U(const uint32_t *d_LU, int64_t m, int64_t n, int64_t l
                            uint32_t *d_U, int64_t ldu, void *stream);
 
 /*
+ * LEU decomposition from the PLUQ (Corollary of the triangularity theorem,
+ * Sec. 3): A = Lbar E Ubar with Lbar = P [L 0; M I_{m-r}] P^T (m x m, unit
+ * lower triangular), E = P diag(I_r, 0) Q (the rank profile matrix, see
+ * rank_profile_matrix) and Ubar = Q^T [U V; 0 0] Q (n x n, upper triangular),
+ * in the original row and column indices.  Inputs are the packed result of
+ * pluq_mod_p (d_LU, stride lda >= n, not modified) with its r, d_perm_p and
+ * d_perm_q.  Either output may be null (not written); d_Lbar has stride
+ * ldl >= m, d_Ubar stride ldu >= n, neither overlaps d_LU.  d_work holds
+ * (m + n) int32 (inverse permutations).  Errors: EINVAL, ENOMEM (workspace).
+ * Asynchronous on `stream`.
+ */
+pluq_status pluq_leu(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                     const int32_t *d_perm_p, const int32_t *d_perm_q, uint32_t *d_Lbar,
+                     int64_t ldl, uint32_t *d_Ubar, int64_t ldu, void *d_work, size_t ws_bytes,
+                     void *stream);
+
+/*
+ * Rank profiles of the leading k x t submatrix of A (0 <= k <= m,
+ * 0 <= t <= n) without forming R (Corollary of Lemma 2, Sec. 4): the ones of
+ * R inside [0, k) x [0, t) are the pivots i < r with perm_p[i] < k and
+ * perm_q[i] < t.  *d_count (device int32) receives their number, the rank of
+ * that submatrix; d_rows / d_cols (capacity r each) receive its row and
+ * column rank profiles, sorted.  Asynchronous on `stream`.
+ */
+pluq_status pluq_leading_rank_profiles(const int32_t *d_perm_p, const int32_t *d_perm_q,
+                                       int64_t m, int64_t n, int64_t r, int64_t k, int64_t t,
+                                       int32_t *d_rows, int32_t *d_cols, int32_t *d_count,
+                                       void *stream);
+
+/*
  * Hot-path kernels of Algorithm 1, callable on their own.
  *
  * MM(C, A, B) of Sec. 2: C <- C - A B mod p (or C <- A B mod p when `assign`

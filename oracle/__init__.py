@@ -203,3 +203,24 @@ def check_pluq(A: np.ndarray, p: int, LU: np.ndarray, perm_p: np.ndarray,
     pq = np.ascontiguousarray(perm_q, dtype=np.int32)
     return int(_load().oracle_check_pluq(_ptr(A, _u32p), m, n, n, p, _ptr(LU, _u32p), n,
                                          _ptr(pp, _i32p), _ptr(pq, _i32p), r))
+
+
+def leu(LU: np.ndarray, perm_p: np.ndarray, perm_q: np.ndarray, r: int):
+    """LEU decomposition read off a PLUQ (Corollary of the triangularity
+    theorem, Sec. 3), written out as its definition:
+        Lbar = P [L 0; M I_{m-r}] P^T,  Ubar = Q^T [U V; 0 0] Q,
+    where P[perm_p[i], i] = 1 and Q[j, perm_q[j]] = 1.  Only entries move; no
+    field arithmetic.  Returns (Lbar m x m, Ubar n x n) as uint32."""
+    LU = np.asarray(LU, dtype=np.int64)
+    m, n = LU.shape
+    inner_l = np.eye(m, dtype=np.int64)                       # [L 0; M I]
+    inner_l[:, :r] = np.tril(LU[:, :r], -1) + np.eye(m, r, dtype=np.int64)
+    inner_u = np.zeros((n, n), dtype=np.int64)                # [U V; 0 0]
+    inner_u[:r, :] = np.triu(LU[:r, :])
+    P = np.zeros((m, m), dtype=np.int64)
+    P[np.asarray(perm_p), np.arange(m)] = 1
+    Q = np.zeros((n, n), dtype=np.int64)
+    Q[np.arange(n), np.asarray(perm_q)] = 1
+    Lbar = P @ inner_l @ P.T                                  # permutation products: entries move
+    Ubar = Q.T @ inner_u @ Q
+    return Lbar.astype(np.uint32), Ubar.astype(np.uint32)

@@ -262,6 +262,12 @@ size_t trsm_workspace(int64_t r, int64_t other, uint32_t p, int kind);
 pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st);
 pluq_status launch_extract(const uint32_t *LU, int64_t lda, int64_t rows, int64_t cols,
                            uint32_t *X, int64_t ldx, bool lower, cudaStream_t st);
+pluq_status launch_leu(const uint32_t *LU, int64_t lda, int64_t m, int64_t n, int64_t r,
+                       const int32_t *perm_p, const int32_t *perm_q, uint32_t *Lbar, int64_t ldl,
+                       uint32_t *Ubar, int64_t ldu, int32_t *work, cudaStream_t st);
+pluq_status launch_leading_profile(const int32_t *pp, const int32_t *pq, int64_t r, int64_t k,
+                                   int64_t t, int32_t *rows, int32_t *cols, int32_t *count,
+                                   cudaStream_t st);
 
 // Leaf (base case) of the recursion.
 constexpr int LEAF_MAX = 128;

@@ -637,6 +637,33 @@ pluq_status pluq_extract_U(const uint32_t *d_LU, int64_t m, int64_t n, int64_t l
     return launch_extract(d_LU, lda, r, n, d_U, ldu, false, (cudaStream_t)stream);
 }
 
+pluq_status pluq_leu(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                     const int32_t *d_perm_p, const int32_t *d_perm_q, uint32_t *d_Lbar,
+                     int64_t ldl, uint32_t *d_Ubar, int64_t ldu, void *d_work, size_t ws_bytes,
+                     void *stream)
+{
+    if (m < 0 || n < 0 || r < 0 || r > m || r > n || lda < n) return PLUQ_EINVAL;
+    if (!d_Lbar && !d_Ubar) return PLUQ_EINVAL;
+    if (m > 0 && n > 0 && !d_LU) return PLUQ_EINVAL;
+    if (d_Lbar && m > 0 && (!d_perm_p || ldl < m)) return PLUQ_EINVAL;
+    if (d_Ubar && n > 0 && (!d_perm_q || ldu < n)) return PLUQ_EINVAL;
+    if (!d_work || ws_bytes < (size_t)(m + n) * sizeof(int32_t)) return PLUQ_ENOMEM;
+    return launch_leu(d_LU, lda, m, n, r, d_perm_p, d_perm_q, d_Lbar, ldl, d_Ubar, ldu,
+                      (int32_t *)d_work, (cudaStream_t)stream);
+}
+
+pluq_status pluq_leading_rank_profiles(const int32_t *d_perm_p, const int32_t *d_perm_q,
+                                       int64_t m, int64_t n, int64_t r, int64_t k, int64_t t,
+                                       int32_t *d_rows, int32_t *d_cols, int32_t *d_count,
+                                       void *stream)
+{
+    if (r < 0 || r > m || r > n || k < 0 || k > m || t < 0 || t > n || !d_count)
+        return PLUQ_EINVAL;
+    if (r > 0 && (!d_perm_p || !d_perm_q || !d_rows || !d_cols)) return PLUQ_EINVAL;
+    return launch_leading_profile(d_perm_p, d_perm_q, r, k, t, d_rows, d_cols, d_count,
+                                  (cudaStream_t)stream);
+}
+
 pluq_status pluq_modmm_workspace_size(int64_t M, int64_t N, int64_t K, uint32_t p, int mm_kind,
                                       size_t *h_bytes)
 {

@@ -154,6 +154,63 @@ __global__ void extract_kernel(const uint32_t *__restrict__ LU, int64_t lda, int
         }
 }
 
+// inv[perm[i]] = i
+__global__ void inverse_perm_kernel(const int32_t *__restrict__ perm, int64_t n,
+                                    int32_t *__restrict__ inv)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) inv[perm[i]] = (int32_t)i;
+}
+
+// LEU read-out (Corollary of the triangularity theorem, Sec. 3), in original
+// row / column indices.  lower: Lbar (m x m) = P [L 0; M I] P^T, entry (a, b)
+// taken at packed position (inv[a], inv[b]); otherwise Ubar (n x n) =
+// Q^T [U V; 0 0] Q, likewise.
+__global__ void leu_kernel(const uint32_t *__restrict__ LU, int64_t lda, int64_t dim, int64_t r,
+                           const int32_t *__restrict__ inv, uint32_t *__restrict__ X, int64_t ldx,
+                           int lower)
+{
+    const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
+    for (int64_t a = blockIdx.y; a < dim; a += gridDim.y) {
+        const int64_t i = inv[a];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int64_t b = c0 + (int64_t)s * GT;
+            if (b >= dim) continue;
+            const int64_t j = inv[b];
+            uint32_t v;
+            if (lower) v = i == j ? 1u : ((j < r && i > j) ? LU[i * lda + j] : 0u);
+            else v = (i < r && j >= i) ? LU[i * lda + j] : 0u;
+            X[a * ldx + b] = v;
+        }
+    }
+}
+
+// Rank profiles of the leading k x t submatrix (Corollary of Lemma 2, Sec. 4):
+// the ones of R inside [0, k) x [0, t) are the pivots i < r with
+// perm_p[i] < k and perm_q[i] < t.  Each selected pivot finds its place among
+// the selected ones by counting smaller rows (columns); *count gets their number.
+__global__ void leading_profile_kernel(const int32_t *__restrict__ pp, const int32_t *__restrict__ pq,
+                                       int64_t r, int64_t k, int64_t t, int32_t *__restrict__ rows,
+                                       int32_t *__restrict__ cols, int32_t *count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r) return;
+    const int32_t ri = pp[i], ci = pq[i];
+    if (ri >= k || ci >= t) return;
+    int64_t pr = 0, pc = 0;
+    for (int64_t u = 0; u < r; ++u) {
+        const int32_t ru = pp[u], cu = pq[u];
+        if (ru < k && cu < t) {
+            pr += ru < ri;
+            pc += cu < ci;
+        }
+    }
+    rows[pr] = ri;
+    cols[pc] = ci;
+    atomicAdd(count, 1);
+}
+
 // Any nonzero in the m x n block?  Blocks OR their finding into words[0] and
 // count themselves in words[1]; the last block publishes the answer to the
 // mapped host words (flag, then sequence number) and clears both counters.
@@ -250,6 +307,36 @@ pluq_status launch_extract(const uint32_t *LU, int64_t lda, int64_t rows, int64_
 {
     if (rows <= 0 || cols <= 0) return PLUQ_OK;
     extract_kernel<<<grid2d(rows, cols), GT, 0, st>>>(LU, lda, rows, cols, X, ldx, lower ? 1 : 0);
+    return last_launch();
+}
+
+pluq_status launch_leu(const uint32_t *LU, int64_t lda, int64_t m, int64_t n, int64_t r,
+                       const int32_t *perm_p, const int32_t *perm_q, uint32_t *Lbar, int64_t ldl,
+                       uint32_t *Ubar, int64_t ldu, int32_t *work, cudaStream_t st)
+{
+    if (Lbar && m > 0) {
+        inverse_perm_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, st>>>(perm_p, m, work);
+        PLUQ_TRY(last_launch());
+        leu_kernel<<<grid2d(m, m), GT, 0, st>>>(LU, lda, m, r, work, Lbar, ldl, 1);
+        PLUQ_TRY(last_launch());
+    }
+    if (Ubar && n > 0) {
+        inverse_perm_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(perm_q, n, work + m);
+        PLUQ_TRY(last_launch());
+        leu_kernel<<<grid2d(n, n), GT, 0, st>>>(LU, lda, n, r, work + m, Ubar, ldu, 0);
+        PLUQ_TRY(last_launch());
+    }
+    return PLUQ_OK;
+}
+
+pluq_status launch_leading_profile(const int32_t *pp, const int32_t *pq, int64_t r, int64_t k,
+                                   int64_t t, int32_t *rows, int32_t *cols, int32_t *count,
+                                   cudaStream_t st)
+{
+    PLUQ_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), st));
+    if (r <= 0) return PLUQ_OK;
+    leading_profile_kernel<<<(unsigned)ceil_div(r, 256), 256, 0, st>>>(pp, pq, r, k, t, rows,
+                                                                      cols, count);
     return last_launch();
 }
 

@@ -41,6 +41,10 @@ _SIGS = {
     "rank_profile_matrix": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp]),
     "pluq_extract_L": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _c_i64, _vp]),
     "pluq_extract_U": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _c_i64, _vp]),
+    "pluq_leu": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp, _vp, _c_i64, _vp,
+                                _c_i64, _vp, ctypes.c_size_t, _vp]),
+    "pluq_leading_rank_profiles": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64,
+                                                  _vp, _vp, _vp, _vp]),
     "pluq_modmm_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _c_u32, ctypes.c_int,
                                                  _szp]),
     "pluq_modmm": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _c_i64, _c_i64, _c_i64,
@@ -211,6 +215,36 @@ def pluq_extract_U(LU: torch.Tensor, r: int, stream=None) -> torch.Tensor:
     _check(load().pluq_extract_U(_ptr(LU), m, n, LU.stride(0), r, _ptr(U), max(n, 1),
                                  _stream(stream)), "pluq_extract_U")
     return U
+
+
+def pluq_leu(LU: torch.Tensor, perm_p: torch.Tensor, perm_q: torch.Tensor, r: int, stream=None):
+    """(Lbar, Ubar) of the LEU decomposition A = Lbar E Ubar; E is the rank
+    profile matrix (rank_profile_matrix)."""
+    _need_cuda(LU, perm_p, perm_q)
+    m, n = LU.shape
+    Lbar = torch.empty((m, m), dtype=LU.dtype, device=LU.device)
+    Ubar = torch.empty((n, n), dtype=LU.dtype, device=LU.device)
+    work = torch.empty(max(m + n, 1), dtype=torch.int32, device=LU.device)
+    _check(load().pluq_leu(_ptr(LU), m, n, LU.stride(0) if m else max(n, 1), r, _ptr(perm_p),
+                           _ptr(perm_q), _ptr(Lbar), max(m, 1), _ptr(Ubar), max(n, 1),
+                           _ptr(work), work.numel() * 4, _stream(stream)), "pluq_leu")
+    return Lbar, Ubar
+
+
+def pluq_leading_rank_profiles(perm_p: torch.Tensor, perm_q: torch.Tensor, r: int, k: int, t: int,
+                               stream=None):
+    """(rows, cols): the row and column rank profiles of the leading k x t
+    submatrix, read from P and Q without forming R; len(rows) is its rank."""
+    _need_cuda(perm_p, perm_q)
+    rows = torch.empty(max(r, 1), dtype=torch.int32, device=perm_p.device)
+    cols = torch.empty(max(r, 1), dtype=torch.int32, device=perm_p.device)
+    count = torch.zeros(1, dtype=torch.int32, device=perm_p.device)
+    _check(load().pluq_leading_rank_profiles(_ptr(perm_p), _ptr(perm_q), perm_p.numel(),
+                                             perm_q.numel(), r, k, t, _ptr(rows), _ptr(cols),
+                                             _ptr(count), _stream(stream)),
+           "pluq_leading_rank_profiles")
+    c = int(count.item())
+    return rows[:c], cols[:c]
 
 
 def modmm_workspace_size(M: int, N: int, K: int, p: int, mm: str = "auto") -> int:

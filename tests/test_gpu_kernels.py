@@ -238,6 +238,33 @@ def test_extract_factors(m, n, r, p):
     assert np.array_equal(prod, Ap)
 
 
+@pytest.mark.parametrize("m,n,r,p", [(120, 90, 50, 65521), (64, 64, 64, 2147483647),
+                                     (33, 70, 0, 7), (200, 150, 150, 8388593)])
+def test_leu_and_leading_profiles(m, n, r, p):
+    """LEU read-out bit-exact with the oracle's (its definition), and the rank
+    profiles of leading k x t blocks, read from P and Q, equal the oracle's
+    row-echelon rank profile of A[:k, :t]."""
+    A, _ = W.planted(m, n, r, p, seed=3 * m + n + r)
+    LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+    d = dev(A)
+    pp, pq, rk = pluq.pluq_mod_p(d, p)
+    assert rk == r0
+    Lb, Ub = pluq.pluq_leu(d, pp, pq, rk)
+    Lb0, Ub0 = oracle.leu(LU0, pp0, pq0, r0)
+    assert np.array_equal(host(Lb), Lb0)
+    assert np.array_equal(host(Ub), Ub0)
+    g = np.random.Generator(np.random.PCG64(m * n + 1))
+    blocks = [(m, n), (0, n), (m, 0), (1, 1)] + [(int(g.integers(0, m + 1)), int(g.integers(0, n + 1)))
+                                                 for _ in range(8)]
+    for (k, t) in blocks:
+        rows, cols = pluq.pluq_leading_rank_profiles(pp, pq, rk, k, t)
+        col = oracle.rank_profile(A[:k, :t], p) if k and t else np.zeros(0, np.int32)
+        want_rows = np.nonzero(col >= 0)[0]
+        want_cols = np.sort(col[col >= 0])
+        assert np.array_equal(rows.cpu().numpy(), want_rows), (k, t)
+        assert np.array_equal(cols.cpu().numpy(), want_cols), (k, t)
+
+
 def test_extract_errors():
     d = torch.zeros((4, 5), dtype=torch.int32, device="cuda")
     with pytest.raises(pluq.PluqError):

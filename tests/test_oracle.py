@@ -202,6 +202,41 @@ def test_leu_theorem_random():
             assert np.array_equal(Ubar, np.triu(Ubar))
 
 
+def test_oracle_leu_pinned():
+    """oracle.leu against the Corollary's properties, not against itself:
+    Lbar unit lower, Ubar upper, Lbar E Ubar = A with E the rank profile matrix
+    from the independent row-echelon routine, and for a generic matrix (all
+    leading minors nonzero, so P = Q = I) the plain [L 0; M I] and [U V; 0 0]."""
+    g = np.random.Generator(np.random.PCG64(78))
+    for it in range(40):
+        p = int(g.choice(PRIMES))
+        m, n = int(g.integers(1, 25)), int(g.integers(1, 25))
+        A = _structured(g, m, n, p)
+        LU, pp, pq, r = oracle.pluq(A, p)
+        Lb, Ub = oracle.leu(LU, pp, pq, r)
+        Lb = Lb.astype(np.int64)
+        Ub = Ub.astype(np.int64)
+        assert np.array_equal(Lb, np.tril(Lb)) and np.all(np.diagonal(Lb) == 1)
+        assert np.array_equal(Ub, np.triu(Ub))
+        col = oracle.rank_profile(A, p)
+        E = np.zeros((m, n), dtype=object)
+        for i, c in enumerate(col):
+            if c >= 0:
+                E[i, c] = 1
+        rec = (Lb.astype(object).dot(E).dot(Ub.astype(object))) % p
+        assert np.array_equal(rec, A.astype(object) % p), (m, n, p)
+    # generic: leading minors nonzero -> P = Q = I
+    p = 65521
+    n = 12
+    L0 = np.tril(g.integers(0, p, (n, n)), -1) + np.eye(n, dtype=np.int64)
+    U0 = np.triu(g.integers(1, p, (n, n)))
+    A = (L0.astype(object).dot(U0.astype(object)) % p).astype(np.uint32)
+    LU, pp, pq, r = oracle.pluq(A, p)
+    Lb, Ub = oracle.leu(LU, pp, pq, r)
+    assert np.array_equal(pp, np.arange(n)) and np.array_equal(pq, np.arange(n))
+    assert np.array_equal(Lb.astype(np.int64), L0) and np.array_equal(Ub.astype(np.int64), U0)
+
+
 # ------------------------------------------------------- planted / sizes --
 
 @pytest.mark.parametrize("m,n,r,p", [(50, 60, 20, 65521), (64, 64, 64, 8388593),
