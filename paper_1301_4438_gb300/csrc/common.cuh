@@ -258,6 +258,8 @@ pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t 
 pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, int64_t r,
                              Field F, int kind, Arena &ar, cudaStream_t st);
 size_t trsm_workspace(int64_t r, int64_t other, uint32_t p, int kind);
+// true when a triangle of r rows is solved directly (no workspace used)
+bool trsm_direct_for(int64_t r);
 
 pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st);
 pluq_status launch_extract(const uint32_t *LU, int64_t lda, int64_t rows, int64_t cols,

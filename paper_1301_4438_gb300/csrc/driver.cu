@@ -146,6 +146,8 @@ struct Ctx {
     int32_t *d_rank;      // device words: range check flag, leaf info
     HostWords *hw;
     int64_t leaf = 128;   // blocks with both sides <= leaf go to the leaf kernel
+    cudaStream_t side = nullptr;            // second stream for independent work of a node
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t leaves = 0;
     int64_t zero_checks = 0;
 };
@@ -272,14 +274,54 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
     PLUQ_TRY(permute_block(c, at(0, h), lda, k, n - h, vec(p1, s1.pid), nullptr));
     PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, h, nullptr, vec(q1, s1.qid)));
-    // D <- L1^{-1} B1 ; E <- C1 U1^{-1}
-    PLUQ_TRY(trsm_left_lower_unit(A, lda, Blk{at(0, h), lda}, r1, n - h, F, c.kind, c.ar, c.st));
-    PLUQ_TRY(trsm_right_upper(A, lda, Blk{at(k, 0), lda}, m - k, r1, F, c.kind, c.ar, c.st));
-    // [F;H] <- [B2;A4] - [M1;E] D ; G <- C2 - E V1
-    PLUQ_TRY(launch_mm(c.kind, Blk{at(r1, h), lda}, at(r1, 0), lda, at(0, h), lda, m - r1, n - h,
-                       r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
-    PLUQ_TRY(launch_mm(c.kind, Blk{at(k, r1), lda}, at(k, 0), lda, at(0, r1), lda, m - k, h - r1,
-                       r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+    // D <- L1^{-1} B1 ; E <- C1 U1^{-1}, then [F;H] <- [B2;A4] - [M1;E] D and
+    // G <- C2 - E V1: each pair is independent (disjoint outputs, shared
+    // read-only operands).  The second of a pair runs on the side stream when
+    // the arena has room for both scratch areas side by side.
+    {
+        const uint32_t p = F.p;
+        const size_t needL = trsm_direct_for(r1) ? 0 : trsm_workspace(r1, n - h, p, c.kind);
+        const size_t needR = trsm_direct_for(r1) ? 0 : trsm_workspace(r1, m - k, p, c.kind);
+        Arena a2 = c.ar;
+        a2.off = align_up(c.ar.off + needL, 1024);
+        const bool both = r1 > 0 && n - h > 0 && m - k > 0;
+        if (c.side && both && a2.off + needR <= c.ar.size) {
+            PLUQ_CUDA_TRY(cudaEventRecord(c.ev_fork, c.st));
+            PLUQ_CUDA_TRY(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+            PLUQ_TRY(trsm_left_lower_unit(A, lda, Blk{at(0, h), lda}, r1, n - h, F, c.kind, c.ar, c.st));
+            PLUQ_TRY(trsm_right_upper(A, lda, Blk{at(k, 0), lda}, m - k, r1, F, c.kind, a2, c.side));
+            PLUQ_CUDA_TRY(cudaEventRecord(c.ev_join, c.side));
+            PLUQ_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_join, 0));
+        } else {
+            PLUQ_TRY(trsm_left_lower_unit(A, lda, Blk{at(0, h), lda}, r1, n - h, F, c.kind, c.ar, c.st));
+            PLUQ_TRY(trsm_right_upper(A, lda, Blk{at(k, 0), lda}, m - k, r1, F, c.kind, c.ar, c.st));
+        }
+    }
+    {
+        const uint32_t p = F.p;
+        const bool tc = c.kind != PLUQ_MM_SIMT;
+        const size_t need1 = tc ? mm_tc_workspace(m - r1, n - h, r1, p, 1) : 0;
+        const size_t need2 = tc ? mm_tc_workspace(m - k, h - r1, r1, p, 1) : 0;
+        Arena a2 = c.ar;
+        a2.off = align_up(c.ar.off + need1, 1024);
+        const bool both = r1 > 0 && m - r1 > 0 && n - h > 0 && m - k > 0 && h - r1 > 0;
+        cudaStream_t s2 = c.st;
+        if (c.side && both && a2.off + need2 <= c.ar.size) {
+            PLUQ_CUDA_TRY(cudaEventRecord(c.ev_fork, c.st));
+            PLUQ_CUDA_TRY(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
+            s2 = c.side;
+        } else {
+            a2 = c.ar;
+        }
+        PLUQ_TRY(launch_mm(c.kind, Blk{at(r1, h), lda}, at(r1, 0), lda, at(0, h), lda, m - r1,
+                           n - h, r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+        PLUQ_TRY(launch_mm(c.kind, Blk{at(k, r1), lda}, at(k, 0), lda, at(0, r1), lda, m - k,
+                           h - r1, r1, F, MM_SUB, 1, 0, 0, 0, a2, s2));
+        if (s2 != c.st) {
+            PLUQ_CUDA_TRY(cudaEventRecord(c.ev_join, c.side));
+            PLUQ_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_join, 0));
+        }
+    }
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
     Res s2, s3;
     PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1, deficient));
@@ -455,6 +497,20 @@ pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p
     c.ar.off = 0;
     c.hw = hw;
     c.leaf = leaf_size();
+    // the side stream and its two events live for this decomposition only
+    struct SideGuard {
+        Ctx &c;
+        ~SideGuard()
+        {
+            if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+            if (c.ev_join) cudaEventDestroy(c.ev_join);
+            if (c.side) cudaStreamDestroy(c.side);
+        }
+    } side_guard{c};
+    if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return PLUQ_ECUDA;
 
     // every entry must already be reduced: checked before anything is written
     int32_t flag = 0;

@@ -353,6 +353,8 @@ size_t trsm_workspace(int64_t r, int64_t other, uint32_t p, int kind)
     return w;
 }
 
+bool trsm_direct_for(int64_t r) { return r <= WR; }
+
 pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t r, int64_t N,
                                  Field F, int kind, Arena &ar, cudaStream_t st)
 {
