@@ -134,23 +134,49 @@ pluq_status wait_words(HostWords *hw, int32_t seq, cudaStream_t st, int at = 0)
 constexpr int ZBASE = 8, ZDEPTH = 27;
 
 struct Ctx {
-    Field F;
-    int kind;
-    cudaStream_t st;
-    Arena ar;             // scratch for products / TRSM (stack discipline)
-    uint32_t *gather;     // m*n scratch for permutations
-    uint32_t *icopy;      // copy of I (r3 x r2)
-    int32_t *smap, *tmap; // S and T index maps of the current node
-    int32_t *vstack;      // child permutation vectors (stack discipline)
-    size_t vtop, vcap;
-    int32_t *d_rank;      // device words: range check flag, leaf info
-    HostWords *hw;
+    Field F{};
+    int kind = 0;
+    cudaStream_t st = nullptr;
+    Arena ar;                       // scratch for products / TRSM (stack discipline)
+    uint32_t *gather = nullptr;     // m*n scratch for permutations
+    uint32_t *icopy = nullptr;      // copy of I (r3 x r2)
+    int32_t *smap = nullptr, *tmap = nullptr;   // S and T index maps of the current node
+    int32_t *vstack = nullptr;      // child permutation vectors (stack discipline)
+    size_t vtop = 0, vcap = 0;
+    int32_t *d_rank = nullptr;      // device words: range check flag, leaf info
+    HostWords *hw = nullptr;
     int64_t leaf = 128;   // blocks with both sides <= leaf go to the leaf kernel
     cudaStream_t side = nullptr;            // second stream for independent work of a node
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_done = nullptr;          // end of this context's work (branch contexts)
+    struct BranchPool *pool = nullptr;      // contexts free to run PLUQ(G) on another thread
     int64_t leaves = 0;
     int64_t zero_checks = 0;
 };
+
+// Contexts that can each run one recursive call on a host thread of its own,
+// with their own streams, host words and scratch (sized for a quarter of the
+// matrix: the block G of any node fits).
+struct BranchPool {
+    std::mutex mu;
+    std::vector<Ctx *> free;
+    Ctx *take()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (free.empty()) return nullptr;
+        Ctx *c = free.back();
+        free.pop_back();
+        return c;
+    }
+    void give(Ctx *c)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        free.push_back(c);
+    }
+};
+constexpr int NBRANCH = 3;            // branch contexts per decomposition
+constexpr int64_t BRANCH_MIN = 256;   // both F and G at least this large in each dimension
+constexpr int64_t BRANCH_MATRIX_MIN = 1024;   // matrices below this get no branch contexts
 
 // Leaf size of the recursion (pluq_set_tuning; PLUQ_LEAF in the environment
 // sets the initial value).  Smaller leaves mean less one-SM elimination work
@@ -323,9 +349,43 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
         }
     }
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
+    // PLUQ(F) and PLUQ(G) work on disjoint blocks with their own permutation
+    // vectors: with a free branch context, G runs on another host thread and
+    // stream while this thread does F (the concurrency noted in Sec. 8)
     Res s2, s3;
-    PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1, deficient));
-    PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient));
+    Ctx *bc = nullptr;
+    if (c.pool && k - r1 >= BRANCH_MIN && n - h >= BRANCH_MIN && m - k >= BRANCH_MIN &&
+        h - r1 >= BRANCH_MIN)
+        bc = c.pool->take();
+    if (bc) {
+        pluq_status sg = PLUQ_OK, sf = PLUQ_OK;
+        if (cudaEventRecord(c.ev_fork, c.st) != cudaSuccess ||
+            cudaStreamWaitEvent(bc->st, c.ev_fork, 0) != cudaSuccess) {
+            c.pool->give(bc);
+            return PLUQ_ECUDA;
+        }
+        std::thread th;
+        bool spawned = true;
+        try {
+            th = std::thread([&] {
+                sg = rec(*bc, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient);
+            });
+        } catch (...) {
+            spawned = false;    // no thread to be had: G on this thread, on bc's stream
+        }
+        sf = rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1, deficient);
+        if (spawned) th.join();
+        else sg = rec(*bc, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient);
+        const bool ok = cudaEventRecord(bc->ev_done, bc->st) == cudaSuccess &&
+                        cudaStreamWaitEvent(c.st, bc->ev_done, 0) == cudaSuccess;
+        c.pool->give(bc);
+        PLUQ_TRY(sf);
+        PLUQ_TRY(sg);
+        if (!ok) return PLUQ_ECUDA;
+    } else {
+        PLUQ_TRY(rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1, deficient));
+        PLUQ_TRY(rec(c, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient));
+    }
     const int64_t r2 = s2.r, r3 = s3.r;
     int32_t *P2 = vec(p2, s2.pid), *Q2 = vec(q2, s2.qid), *P3 = vec(p3, s3.pid), *Q3 = vec(q3, s3.qid);
     // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
@@ -387,7 +447,7 @@ struct Layout {
     size_t gather, icopy, maps, vstack, small, arena, total;
 };
 
-Layout layout(int64_t m, int64_t n, uint32_t p, int kind)
+Layout layout_core(int64_t m, int64_t n, uint32_t p, int kind)
 {
     Layout L{};
     const int64_t mn = m < n ? m : n;
@@ -401,6 +461,44 @@ Layout layout(int64_t m, int64_t n, uint32_t p, int kind)
     L.arena = align_up(L.arena + (1 << 20), 256);
     L.total = L.gather + L.icopy + L.maps + L.vstack + L.small + L.arena;
     return L;
+}
+
+bool has_branches(int64_t m, int64_t n) { return m >= BRANCH_MATRIX_MIN && n >= BRANCH_MATRIX_MIN; }
+
+// the main context, then NBRANCH branch contexts for ceil(m/2) x ceil(n/2)
+struct Layout2 {
+    Layout main, branch;
+    size_t total;
+};
+Layout2 layout(int64_t m, int64_t n, uint32_t p, int kind, bool branches = true)
+{
+    Layout2 L{};
+    L.main = layout_core(m, n, p, kind);
+    L.total = L.main.total;
+    if (branches && has_branches(m, n)) {
+        L.branch = layout_core((m + 1) / 2, (n + 1) / 2, p, kind);
+        L.total += NBRANCH * L.branch.total;
+    }
+    return L;
+}
+
+// carve one context's scratch out of w (advancing w)
+void carve(Ctx &c, const Layout &L, int64_t m, char *&w)
+{
+    c.gather = (uint32_t *)w; w += L.gather;
+    c.icopy = (uint32_t *)w; w += L.icopy;
+    c.smap = (int32_t *)w;
+    c.tmap = c.smap + m;
+    w += L.maps;
+    c.vstack = (int32_t *)w;
+    c.vcap = L.vstack / 4;
+    c.vtop = 0;
+    w += L.vstack;
+    c.d_rank = (int32_t *)w; w += L.small;
+    c.ar.base = w;
+    c.ar.size = L.arena;
+    c.ar.off = 0;
+    w += L.arena;
 }
 
 int resolve_kind(int kind)
@@ -469,9 +567,9 @@ namespace {
 // One decomposition on `st` with scratch at `w` (validated by the caller).
 pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,
                     int32_t *d_perm_p, int32_t *d_perm_q, int64_t *h_rank, char *w, int kind,
-                    cudaStream_t st, HostWords *hw)
+                    cudaStream_t st, HostWords *hw, bool branches)
 {
-    Layout L = layout(m, n, p, kind);
+    Layout2 L = layout(m, n, p, kind, branches);
     *h_rank = 0;
     if (m == 0 || n == 0) {
         PLUQ_TRY(launch_iota(d_perm_p, m, st));
@@ -482,35 +580,57 @@ pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p
     c.F = make_field(p);
     c.kind = kind;
     c.st = st;
-    c.gather = (uint32_t *)w; w += L.gather;
-    c.icopy = (uint32_t *)w; w += L.icopy;
-    c.smap = (int32_t *)w;
-    c.tmap = c.smap + m;
-    w += L.maps;
-    c.vstack = (int32_t *)w;
-    c.vcap = L.vstack / 4;
-    c.vtop = 0;
-    w += L.vstack;
-    c.d_rank = (int32_t *)w; w += L.small;
-    c.ar.base = w;
-    c.ar.size = L.arena;
-    c.ar.off = 0;
+    carve(c, L.main, m, w);
     c.hw = hw;
     c.leaf = leaf_size();
-    // the side stream and its two events live for this decomposition only
-    struct SideGuard {
+    // streams, events and host words of this decomposition's contexts live
+    // until it returns
+    Ctx branch[NBRANCH];
+    BranchPool pool;
+    struct Guard {
         Ctx &c;
-        ~SideGuard()
+        Ctx *b;
+        ~Guard()
         {
-            if (c.ev_fork) cudaEventDestroy(c.ev_fork);
-            if (c.ev_join) cudaEventDestroy(c.ev_join);
-            if (c.side) cudaStreamDestroy(c.side);
+            auto drop = [](Ctx &x, bool own_stream) {
+                if (x.ev_fork) cudaEventDestroy(x.ev_fork);
+                if (x.ev_join) cudaEventDestroy(x.ev_join);
+                if (x.ev_done) cudaEventDestroy(x.ev_done);
+                if (x.side) cudaStreamDestroy(x.side);
+                if (own_stream && x.st) cudaStreamDestroy(x.st);
+            };
+            drop(c, false);
+            for (int i = 0; i < NBRANCH; ++i) {
+                drop(b[i], true);
+                if (b[i].hw) release_words(b[i].hw);
+            }
         }
-    } side_guard{c};
-    if (cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming) != cudaSuccess)
-        return PLUQ_ECUDA;
+    } guard{c, branch};
+    auto make_streams = [](Ctx &x) {
+        return cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&x.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&x.ev_join, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&x.ev_done, cudaEventDisableTiming) == cudaSuccess;
+    };
+    if (!make_streams(c)) return PLUQ_ECUDA;
+    if (branches && has_branches(m, n)) {
+        for (int i = 0; i < NBRANCH; ++i) {
+            Ctx &b = branch[i];
+            b.F = c.F;
+            b.kind = kind;
+            b.leaf = c.leaf;
+            if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess ||
+                !make_streams(b))
+                return PLUQ_ECUDA;
+            b.hw = acquire_words();
+            if (!b.hw) return PLUQ_ECUDA;
+            carve(b, L.branch, (m + 1) / 2, w);
+            PLUQ_CUDA_TRY(cudaMemsetAsync(b.d_rank, 0, 64, st));
+            b.pool = &pool;
+            pool.free.push_back(&b);
+        }
+        c.pool = &pool;
+    }
 
     // every entry must already be reduced: checked before anything is written
     int32_t flag = 0;
@@ -558,7 +678,7 @@ pluq_status pluq_mod_p(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_
     HostWords *hw = acquire_words();
     if (!hw) return PLUQ_ECUDA;
     pluq_status s = run_one(d_A, m, n, lda, p, d_perm_p, d_perm_q, h_rank, (char *)d_work, kind,
-                            (cudaStream_t)stream, hw);
+                            (cudaStream_t)stream, hw, true);
     release_words(hw);
     return s;
 }
@@ -571,7 +691,7 @@ pluq_status pluq_batched_workspace_size(const int64_t *h_m, const int64_t *h_n, 
     size_t mx = 0;
     for (int64_t i = 0; i < count; ++i) {
         if (h_m[i] < 0 || h_n[i] < 0) return PLUQ_EINVAL;
-        const size_t w = layout(h_m[i], h_n[i], p, PLUQ_MM_TENSOR).total;
+        const size_t w = layout(h_m[i], h_n[i], p, PLUQ_MM_TENSOR, false).total;
         if (w > mx) mx = w;
     }
     const int64_t used = count < workers ? (count > 0 ? count : 1) : workers;
@@ -634,7 +754,7 @@ pluq_status pluq_mod_p_batched(uint32_t *const *h_dA, const int64_t *h_m, const 
                 if (q >= count) break;
                 const int64_t i = order[q];
                 pluq_status s = run_one(h_dA[i], h_m[i], h_n[i], h_lda[i], p, h_dperm_p[i],
-                                        h_dperm_q[i], &h_rank[i], w, kind, st, hw);
+                                        h_dperm_q[i], &h_rank[i], w, kind, st, hw, false);
                 if (s != PLUQ_OK) {
                     int expect = PLUQ_OK;
                     first_err.compare_exchange_strong(expect, (int)s);

@@ -17,12 +17,16 @@ struct Rec {
     cudaEvent_t a, b;
     int cls;
     double work;
+    bool done;
 };
 std::mutex mu;
 std::vector<Rec> recs;   // event pairs, reused across sessions
 size_t used = 0;
-cudaEvent_t pending_start[NCLS];
-bool has_pending[NCLS];
+// the open record of each class, per host thread (recursion branches and batch
+// workers launch from several threads at once)
+thread_local long open_rec[NCLS] = {-1, -1, -1, -1, -1, -1};
+thread_local unsigned open_session[NCLS] = {0, 0, 0, 0, 0, 0};
+unsigned session = 1;
 }  // namespace
 
 void start(int cls, cudaStream_t st)
@@ -37,28 +41,31 @@ void start(int cls, cudaStream_t st)
     Rec &r = recs[used];
     r.cls = cls;
     r.work = 0;
+    r.done = false;
     cudaEventRecord(r.a, st);
-    has_pending[cls] = true;
-    pending_start[cls] = r.a;
+    open_rec[cls] = (long)used;
+    open_session[cls] = session;
+    ++used;
 }
 
 void stop(int cls, cudaStream_t st, double work)
 {
     if (!((g_on.load(std::memory_order_relaxed) >> cls) & 1)) return;
     std::lock_guard<std::mutex> lk(mu);
-    if (used >= recs.size() || !has_pending[cls]) return;
-    Rec &r = recs[used];
+    const long i = open_rec[cls];
+    if (i < 0 || open_session[cls] != session || (size_t)i >= used) return;
+    Rec &r = recs[i];
     r.work = work;
     cudaEventRecord(r.b, st);
-    has_pending[cls] = false;
-    ++used;
+    r.done = true;
+    open_rec[cls] = -1;
 }
 
 void begin_session()
 {
     std::lock_guard<std::mutex> lk(mu);
     used = 0;
-    for (int c = 0; c < NCLS; ++c) has_pending[c] = false;
+    ++session;
 }
 
 int read(int cls, long long *launches, double *ms, double *work)
@@ -67,7 +74,7 @@ int read(int cls, long long *launches, double *ms, double *work)
     long long n = 0;
     double t = 0, w = 0;
     for (size_t i = 0; i < used; ++i) {
-        if (recs[i].cls != cls) continue;
+        if (recs[i].cls != cls || !recs[i].done) continue;
         if (cudaEventSynchronize(recs[i].b) != cudaSuccess) return -1;
         float e = 0;
         if (cudaEventElapsedTime(&e, recs[i].a, recs[i].b) != cudaSuccess) return -1;
