@@ -355,66 +355,69 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
     for (int j0 = 0; j0 < kmax; j0 += PB) {
         const int b = kmax - j0 < PB ? kmax - j0 : PB;
         const int R = m - j0;                        // panel rows
-        const int pw = (R + 31) / 32;                // warps holding them (<= 4)
+        // four lanes per panel row, four of the panel's columns each: eight rows
+        // per warp, pw warps (<= 16) hold the panel
+        const int pw = (R + 7) / 8;
         // (1) fraction-free elimination of the panel columns
         if (warp < pw) {
-            const int rel = warp * 32 + lane;        // this lane's panel row
+            const int sub = lane & 3;                // this lane's columns 4 sub .. 4 sub + 3
+            const int rel = warp * 8 + (lane >> 2);  // this lane's panel row
             const bool act = rel < R;
-            uint32_t w[PB];
+            uint32_t w[4];
 #pragma unroll
-            for (int c = 0; c < PB; ++c) w[c] = (act && c < b) ? W[(j0 + rel) * LD + j0 + c] : 0u;
-            // the step loop stays rolled (straight-line code executed once per
-            // panel would be fetch bound); the column loop is unrolled with
+            for (int u = 0; u < 4; ++u) {
+                const int c = 4 * sub + u;
+                w[u] = (act && c < b) ? W[(j0 + rel) * LD + j0 + c] : 0u;
+            }
+            // the step loop stays rolled; the four column slots are unrolled with
             // predicated bodies, so w stays in registers
             bool fail = false;
 #pragma unroll 1
             for (int k = 0; k < b && !fail; ++k) {
-                if (warp == 0 && lane == k) {
+                if (rel == k) {
 #pragma unroll
-                    for (int c = 0; c < PB; ++c) S.pbuf[k & 1][c] = w[c];
+                    for (int u = 0; u < 4; ++u) S.pbuf[k & 1][4 * sub + u] = w[u];
                 }
                 if (pw > 1) asm volatile("bar.sync 1, %0;" ::"r"(pw * 32) : "memory");
                 else __syncwarp();
-                // the pivot row in registers before any update uses it
-                uint32_t q[PB];
+                uint32_t q[4];
 #pragma unroll
-                for (int c = 0; c < PB; ++c) q[c] = S.pbuf[k & 1][c];
+                for (int u = 0; u < 4; ++u) q[u] = S.pbuf[k & 1][4 * sub + u];
                 const uint32_t d = S.pbuf[k & 1][k];
                 fail = d == 0;
+                if (tid == 0) S.dval[k] = d;
+                // this row's value in column k sits in slot k & 3 of lane k >> 2 of the quad
+                uint32_t mine = w[0];
+#pragma unroll
+                for (int u = 1; u < 4; ++u)
+                    if ((k & 3) == u) mine = w[u];
+                const uint32_t fk = __shfl_sync(0xFFFFFFFFu, mine, (lane & ~3) | (k >> 2));
                 if (!fail && act && rel > k) {
-                    uint32_t fk = 0;
 #pragma unroll
-                    for (int c = 0; c < PB; ++c)
-                        if (c == k) fk = w[c];
-                    // computed for every column and kept by a select: the
-                    // independent updates overlap instead of running as one
-                    // branch after another
-#pragma unroll
-                    for (int c = 1; c < PB; ++c) {
-                        const uint32_t nv = ff_update<SMALLP>(d, w[c], fk, q[c], F, F32);
-                        w[c] = (c > k && c < b) ? nv : w[c];
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 4 * sub + u;
+                        const uint32_t nv = ff_update<SMALLP>(d, w[u], fk, q[u], F, F32);
+                        w[u] = (c > k && c < b) ? nv : w[u];
                     }
                 }
             }
             if (fail) {
                 if (tid == 0) S.gfail = 1;
             } else {
-                // (2) row k (lane k of warp 0) holds d_k = w[k], untouched since
-                // step k.  One inversion serves the panel: with D = prod d_k,
+                // (2) one inversion serves the panel: with D = prod d_k,
                 // c_k = prod_{j<k} d_j and s_k = prod_{j>=k} d_j,
-                // 1/d_k = c_k s_{k+1} / D and 1/c_k = s_k / D.
+                // 1/d_k = c_k s_{k+1} / D and 1/c_k = s_k / D
+                if (pw > 1) asm volatile("bar.sync 1, %0;" ::"r"(pw * 32) : "memory");
+                else __syncwarp();
                 if (warp == 0) {
-                    uint32_t dv = 1;
-#pragma unroll
-                    for (int c = 0; c < PB; ++c)
-                        if (c == lane && c < b) dv = w[c];
+                    const uint32_t dv = lane < b ? S.dval[lane] : 1u;
                     uint32_t pre = dv, suf = dv;                        // inclusive scans
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, pre, o);
-                        const uint32_t u = __shfl_down_sync(0xFFFFFFFFu, suf, o);
+                        const uint32_t t = __shfl_down_sync(0xFFFFFFFFu, suf, o);
                         if (lane >= o) pre = scale<SMALLP>(pre, v, F, F32);
-                        if (lane + o < 32) suf = scale<SMALLP>(suf, u, F, F32);
+                        if (lane + o < 32) suf = scale<SMALLP>(suf, t, F, F32);
                     }
                     uint32_t ce = __shfl_up_sync(0xFFFFFFFFu, pre, 1);    // c_lane
                     if (lane == 0) ce = 1;
@@ -438,11 +441,13 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
                 if (act) {
                     const uint32_t ic = rel < b ? S.inv_c[rel] : 0u;
 #pragma unroll
-                    for (int c = 0; c < PB; ++c)
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 4 * sub + u;
                         if (c < b) {
                             const uint32_t sc = c < rel ? S.inv_d[c] : ic;
-                            W[(j0 + rel) * LD + j0 + c] = scale<SMALLP>(w[c], sc, F, F32);
+                            W[(j0 + rel) * LD + j0 + c] = scale<SMALLP>(w[u], sc, F, F32);
                         }
+                    }
                 }
             }
         }
