@@ -55,17 +55,28 @@ __device__ __forceinline__ int first(const Mask &a)
 {
     return a.w[0] ? __ffsll(a.w[0]) - 1 : 64 + __ffsll(a.w[1]) - 1;
 }
-// the lowest `cnt` members of a
+// the lowest k (>= 0) set bits of a 32- / 64-bit word: keep the bits up to
+// the k-th set one, found with __fns (n-th set bit)
+__device__ __forceinline__ uint32_t lowest32(uint32_t x, int k)
+{
+    if (k <= 0) return 0u;
+    if (k >= __popc(x)) return x;
+    const unsigned pos = __fns(x, 0, k);   // position of the k-th set bit
+    return x & (uint32_t)((2ull << pos) - 1ull);
+}
+__device__ __forceinline__ uint64_t lowest64(uint64_t x, int k)
+{
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    const int cl = __popc(lo);
+    if (k <= cl) return lowest32(lo, k);
+    return lo | ((uint64_t)lowest32(hi, k - cl) << 32);
+}
+// the lowest `cnt` members of a, in O(1)
 __device__ __forceinline__ Mask lowest(const Mask &a, int cnt)
 {
-    Mask out{{0, 0}};
-    Mask rest = a;
-    for (int t = 0; t < cnt; ++t) {
-        int i = first(rest);
-        set(out, i);
-        rest.w[i >> 6] &= ~(1ull << (i & 63));
-    }
-    return out;
+    const int c0 = __popcll(a.w[0]);
+    if (cnt <= c0) return Mask{{lowest64(a.w[0], cnt), 0}};
+    return Mask{{a.w[0], lowest64(a.w[1], cnt - c0)}};
 }
 
 // Algorithm 1's order of the ones of R inside rows x cols, as an explicit
@@ -337,21 +348,31 @@ constexpr int PB = 16;   // panel width of the generic path
 // U11; (3) U12 = L11^{-1} A12, one thread per column; (4) A22 -= L21 U12, each
 // element one delayed reduction.  Returns false, with A untouched, at the first
 // zero pivot (the rank profile is not generic).
+//
+// With row / column maps (rowmap[i], colmap[j]: original row and column of
+// position i, j) it factors P^T A Q^T instead, taking kcap pivots: phase 3 of
+// the general path, whose pivots in Algorithm 1's order are nonzero by
+// construction (the leading minors of P^T A Q^T up to order r are products of
+// U's diagonal).  pid / qid are reported as given.
 template <bool SMALLP>
 __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, const Field &F,
                            const Field32 &F32, LeafShared &S, int32_t *perm_p_out,
                            int32_t *perm_q_out, int32_t *info_out, int info_len,
-                           volatile int32_t *host_info, int32_t seq)
+                           volatile int32_t *host_info, int32_t seq,
+                           const int32_t *rowmap = nullptr, const int32_t *colmap = nullptr,
+                           int kcap = -1, int pid = 1, int qid = 1)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = F.p;
     const uint32_t w16 = (uint32_t)((1ull << 16) % p);
     uint32_t *W = S.W;
-    for (int i = warp; i < m; i += NW)
-        for (int j = lane; j < n; j += 32) W[i * LD + j] = A[(int64_t)i * lda + j];
+    for (int i = warp; i < m; i += NW) {
+        const int64_t src = rowmap ? rowmap[i] : i;
+        for (int j = lane; j < n; j += 32) W[i * LD + j] = A[src * lda + (colmap ? colmap[j] : j)];
+    }
     if (tid == 0) S.gfail = 0;
     __syncthreads();
-    const int kmax = m < n ? m : n;
+    const int kmax = kcap >= 0 ? kcap : (m < n ? m : n);
     for (int j0 = 0; j0 < kmax; j0 += PB) {
         const int b = kmax - j0 < PB ? kmax - j0 : PB;
         const int R = m - j0;                        // panel rows
@@ -480,21 +501,23 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
             }
         __syncthreads();
     }
-    // the packed block, P = Q = I, r = min(m, n)
+    // the packed block (every entry is read into W before any is written), the
+    // permutations and r
+    __syncthreads();
     for (int i = warp; i < m; i += NW)
         for (int j = lane; j < n; j += 32) A[(int64_t)i * lda + j] = W[i * LD + j];
-    for (int i = tid; i < m; i += LT) perm_p_out[i] = i;
-    for (int j = tid; j < n; j += LT) perm_q_out[j] = j;
+    for (int i = tid; i < m; i += LT) perm_p_out[i] = rowmap ? rowmap[i] : i;
+    for (int j = tid; j < n; j += LT) perm_q_out[j] = colmap ? colmap[j] : j;
     if (tid == 0) {
         info_out[0] = kmax;
         if (info_len > 2) {
-            info_out[1] = 1;
-            info_out[2] = 1;
+            info_out[1] = pid;
+            info_out[2] = qid;
         }
         if (host_info) {
             host_info[1] = kmax;
-            host_info[2] = 1;
-            host_info[3] = 1;
+            host_info[2] = pid;
+            host_info[3] = qid;
             __threadfence_system();
             host_info[0] = seq;
         }
@@ -709,58 +732,26 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     qid = __syncthreads_and(qid);
 
     // ---------------- phase 3: elimination without pivoting ---------------
+    // P^T A Q^T in Algorithm 1's order by the blocked path (its r leading
+    // pivots are nonzero), which also writes the block, P, Q and r
     if (!same) {
-        // row i of P^T A Q^T in registers (rows warp + NW t, columns lane + 32 s)
-#pragma unroll
-        for (int t = 0; t < RPW; ++t) {
-            const int i = warp + NW * t;
-#pragma unroll
-            for (int s = 0; s < CPL; ++s) {
-                const int j = lane + 32 * s;
-                w[t][s] = (i < m && j < n) ? A[(int64_t)S.perm_p[i] * lda + S.perm_q[j]] : 0u;
-            }
-        }
-        if (warp == 0) {
-#pragma unroll
-            for (int s = 0; s < CPL; ++s) S.pbuf[0][lane + 32 * s] = w[0][s];
-        }
         __syncthreads();
-        for (int k = 0; k < r; ++k) {
-            uint32_t prow[CPL];
-#pragma unroll
-            for (int s = 0; s < CPL; ++s) prow[s] = S.pbuf[k & 1][lane + 32 * s];
-            const uint32_t dk = S.pbuf[k & 1][k];
-            if (tid == 0) S.dval[k] = dk;
-            const int sk = k >> 5, lk = k & 31;
-            const int tk = k < warp ? 0 : (k - warp) / NW + 1;   // first own row below k
-#pragma unroll
-            for (int t = 0; t < RPW; ++t) {
-                if (t < tk) continue;
-                if (t >= tmax) break;
-                const uint32_t f = __shfl_sync(0xFFFFFFFFu, pick<CPL>(w[t], sk), lk);
-#pragma unroll
-                for (int s = 0; s < CPL; ++s) {
-                    const int j = lane + 32 * s;
-                    const uint32_t nv = ff_update<SMALLP>(dk, w[t][s], f, prow[s], F, F32);
-                    w[t][s] = (s < ncl && j > k && j < n) ? nv : w[t][s];
+        if (!generic_lu<SMALLP>(A, m, n, lda, F, F32, S, perm_p_out, perm_q_out, info_out,
+                                info_len, host_info, seq, S.perm_p, S.perm_q, r, pid, qid)) {
+            if (tid == 0) {
+                info_out[0] = -1;   // a zero pivot here contradicts the rank profile found
+                if (host_info) {
+                    host_info[1] = -1;
+                    __threadfence_system();
+                    host_info[0] = seq;
                 }
             }
-            // the owner of row k + 1 publishes it for the next step
-            const int nk = k + 1;
-            if (nk < m && warp == nk % NW) {
-#pragma unroll
-                for (int t = 0; t < RPW; ++t)
-                    if (warp + NW * t == nk) {
-#pragma unroll
-                        for (int s = 0; s < CPL; ++s) S.pbuf[nk & 1][lane + 32 * s] = w[t][s];
-                    }
-            }
-            __syncthreads();
         }
+        return;
     }
 
-    // stage the rows in shared memory (original positions after phase 1,
-    // P^T A Q^T positions after phase 3)
+    // stage the rows in shared memory (original positions, phase 1's order is
+    // Algorithm 1's)
 #pragma unroll
     for (int t = 0; t < RPW; ++t) {
         const int i = warp + NW * t;
