@@ -45,8 +45,17 @@ struct Mask {                  // 128-bit set of row or column indices
     uint64_t w[2];
 };
 __device__ __forceinline__ int popc(const Mask &a) { return __popcll(a.w[0]) + __popcll(a.w[1]); }
-__device__ __forceinline__ bool has(const Mask &a, int i) { return (a.w[i >> 6] >> (i & 63)) & 1; }
-__device__ __forceinline__ void set(Mask &a, int i) { a.w[i >> 6] |= 1ull << (i & 63); }
+// word selection by value, not by index, so that masks can stay in registers
+__device__ __forceinline__ bool has(const Mask &a, int i)
+{
+    return ((i < 64 ? a.w[0] : a.w[1]) >> (i & 63)) & 1;
+}
+__device__ __forceinline__ void set(Mask &a, int i)
+{
+    const uint64_t bit = 1ull << (i & 63);
+    if (i < 64) a.w[0] |= bit;
+    else a.w[1] |= bit;
+}
 __device__ __forceinline__ Mask andnot(const Mask &a, const Mask &b)
 {
     return Mask{{a.w[0] & ~b.w[0], a.w[1] & ~b.w[1]}};
@@ -114,15 +123,21 @@ __device__ int order_pivots(Frame *stk, const int32_t *col_of_row, const int32_t
     Mask prow_mask{{0, 0}};               // rows holding a one of R
     for (int i = 0; i < m; ++i)
         if (col_of_row[i] >= 0) set(prow_mask, i);
+    // The current frame lives in registers: it is copied in once per pass
+    // and written back only when a child is pushed above it (a popped frame is
+    // dropped).  Reading and writing its fields in shared memory one by one was
+    // a chain of dependent accesses on this single thread.
     while (top >= 0) {
-        Frame &f = stk[top];
+        Frame f = stk[top];
         if (f.stage == 0) {
             f.ur = Mask{{0, 0}};
             f.uc = Mask{{0, 0}};
             // ones of R inside the frame, in row order: descent-free?
             bool mono = true;
             int lastc = -1;
-            for (int w = 0; w < 2 && mono; ++w) {
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                if (!mono) break;
                 uint64_t bits = f.rows.w[w] & prow_mask.w[w];
                 while (bits) {
                     const int i = 64 * w + __ffsll(bits) - 1;
@@ -135,6 +150,7 @@ __device__ int order_pivots(Frame *stk, const int32_t *col_of_row, const int32_t
                 }
             }
             if (mono) {
+#pragma unroll
                 for (int w = 0; w < 2; ++w) {
                     uint64_t bits = f.rows.w[w] & prow_mask.w[w];
                     while (bits) {
@@ -176,8 +192,10 @@ __device__ int order_pivots(Frame *stk, const int32_t *col_of_row, const int32_t
             f.cl = lowest(f.cols, nc / 2); f.cr = andnot(f.cols, f.cl);
             f.stage = 1;
             if (top + 1 >= MAX_DEPTH) return -1;
-            Frame &c = stk[top + 1];                       // A1
-            c.rows = f.rt; c.cols = f.cl; c.stage = 0;
+            stk[top] = f;
+            stk[top + 1].rows = f.rt;                      // A1
+            stk[top + 1].cols = f.cl;
+            stk[top + 1].stage = 0;
             ++top;
             continue;
         }
@@ -185,23 +203,26 @@ __device__ int order_pivots(Frame *stk, const int32_t *col_of_row, const int32_t
         f.ur.w[0] |= ret_r.w[0]; f.ur.w[1] |= ret_r.w[1];
         f.uc.w[0] |= ret_c.w[0]; f.uc.w[1] |= ret_c.w[1];
         if (f.stage < 4 && top + 1 >= MAX_DEPTH) return -1;
-        Frame &c = stk[top + 1];
+        Mask crows, ccols;
         if (f.stage == 1) {
             f.r1 = ret_r; f.c1 = ret_c;
-            c.rows = andnot(f.rt, f.r1); c.cols = f.cr;     // F
+            crows = andnot(f.rt, f.r1); ccols = f.cr;      // F
         } else if (f.stage == 2) {
             f.c2 = ret_c;
-            c.rows = f.rb; c.cols = andnot(f.cl, f.c1);     // G
+            crows = f.rb; ccols = andnot(f.cl, f.c1);      // G
         } else if (f.stage == 3) {
             f.r3 = ret_r;
-            c.rows = andnot(f.rb, f.r3); c.cols = andnot(f.cr, f.c2);   // R
+            crows = andnot(f.rb, f.r3); ccols = andnot(f.cr, f.c2);   // R
         } else {
             ret_r = f.ur; ret_c = f.uc;
             --top;
             continue;
         }
         ++f.stage;
-        c.stage = 0;
+        stk[top] = f;
+        stk[top + 1].rows = crows;
+        stk[top + 1].cols = ccols;
+        stk[top + 1].stage = 0;
         ++top;
         if (top >= MAX_DEPTH) return -1;
     }
