@@ -16,10 +16,10 @@
 //     columns not used by A1 (G), and the bottom rows not used by G x right
 //     columns not used by F (R).  A call with one row or one column keeps the
 //     single one of R it contains.
-//  3. Elimination without pivoting on P^T A Q^T in that order.  When the order
-//     of phase 2 equals the row order of phase 1 (always the case for generic
-//     rank profiles), phase 1 already holds this factorisation and phase 3 is
-//     skipped.
+//  3. Elimination without pivoting on P^T A Q^T in that order, by the blocked
+//     path below (its leading pivots up to order r are nonzero).  When the
+//     order of phase 2 equals the row order of phase 1, phase 1 already holds
+//     this factorisation and phase 3 is skipped.
 // Before phase 1 the kernel tries the generic case: when every leading
 // principal minor of order <= min(m, n) is nonzero, R is the identity pattern
 // (rho(k, t) = min(k, t)), Algorithm 1 meets the pivots on the diagonal and
@@ -791,16 +791,17 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     }
     __syncthreads();
 
-    // write the packed block [L\U V; M 0] in P, Q order
+    // write the packed block [L\U V; M 0] in P, Q order (phase 1's rows are in
+    // original positions, its pivots in Algorithm 1's order)
     for (int e = tid; e < m * LM; e += LT) {
         const int i = e / LM, j = e % LM;
         if (j >= n) continue;
         uint32_t v;
         if (i < r && j >= i) {
-            uint32_t x = same ? S.W[S.piv_row[i] * LD + S.perm_q[j]] : S.W[i * LD + j];
+            const uint32_t x = S.W[S.piv_row[i] * LD + S.perm_q[j]];
             v = mul_mod(x, S.inv_c[i], F);
         } else if (j < r && i > j) {
-            uint32_t x = same ? S.W[S.perm_p[i] * LD + S.piv_col[j]] : S.W[i * LD + j];
+            const uint32_t x = S.W[S.perm_p[i] * LD + S.piv_col[j]];
             v = mul_mod(x, S.inv_d[j], F);
         } else {
             v = 0;
@@ -844,7 +845,6 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     const int rpw = m <= 32 ? 2 : m <= 64 ? 4 : 8;
     const bool small = F.p <= 65536u;
     prof::start(prof::LEAF, st);
-    pluq_status ls = PLUQ_OK;
 #define PLUQ_LEAF_CASE(SP, C, R)                                                                  \
     if (small == SP && cpl == C && rpw == R) {                                                   \
         static const bool attr = cudaFuncSetAttribute(leaf_kernel<SP, C, R>,                     \
@@ -862,7 +862,6 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     PLUQ_LEAF_CASE(false, 2, 2) PLUQ_LEAF_CASE(false, 2, 4) PLUQ_LEAF_CASE(false, 2, 8)
     PLUQ_LEAF_CASE(false, 4, 2) PLUQ_LEAF_CASE(false, 4, 4) PLUQ_LEAF_CASE(false, 4, 8)
 #undef PLUQ_LEAF_CASE
-    (void)ls;
     pluq_status s = last_launch();
     // algorithmic work: the field operations of eliminating the block at full
     // rank, 2 m n k - (m + n) k^2 + 2/3 k^3 with k = min(m, n)
