@@ -75,6 +75,12 @@ def _load():
                                               ctypes.c_int64, ctypes.c_uint32, _u32p,
                                               ctypes.c_int64, _i32p, _i32p, ctypes.c_int64]
             lib.oracle_check_pluq.restype = ctypes.c_int
+            lib.oracle_rref.argtypes = [_u32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_uint32, _i32p]
+            lib.oracle_rref.restype = ctypes.c_int64
+            lib.oracle_determinant.argtypes = [_u32p, ctypes.c_int64, ctypes.c_int64,
+                                               ctypes.c_uint32, _u32p]
+            lib.oracle_determinant.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -224,3 +230,79 @@ def leu(LU: np.ndarray, perm_p: np.ndarray, perm_q: np.ndarray, r: int):
     Lbar = P @ inner_l @ P.T                                  # permutation products: entries move
     Ubar = Q.T @ inner_u @ Q
     return Lbar.astype(np.uint32), Ubar.astype(np.uint32)
+
+
+# ------------------------------------------------ uses of the decomposition --
+# Sec. 1 lists solving linear systems, the determinant and the nullspace among
+# the uses of a triangular decomposition.  These are computed here from their
+# textbook definitions (Gauss-Jordan RREF, elimination with row exchanges),
+# independently of any PLUQ.
+
+
+def rref(A: np.ndarray, p: int, npiv: int = None):
+    """Reduced row echelon form of A (m x n); pivots only among the first
+    npiv columns (default n).  Returns (E, pivot columns)."""
+    E = _u32(A).copy()
+    m, n = E.shape
+    npiv = n if npiv is None else npiv
+    pc = np.zeros(max(min(m, npiv), 1), dtype=np.int32)
+    if m == 0 or n == 0:
+        return E, pc[:0].copy()
+    r = _load().oracle_rref(_ptr(E, _u32p), m, n, n, npiv, p, _ptr(pc, _i32p))
+    if r < 0:
+        raise OracleError(int(r), "rref")
+    return E, pc[:r].copy()
+
+
+def determinant(A: np.ndarray, p: int) -> int:
+    """det A mod p for square A (1 for the 0 x 0 matrix)."""
+    A = _u32(A)
+    n, n2 = A.shape
+    assert n == n2
+    if n == 0:
+        return 1
+    d = np.zeros(1, dtype=np.uint32)
+    st = _load().oracle_determinant(_ptr(A, _u32p), n, n, p, _ptr(d, _u32p))
+    if st != 0:
+        raise OracleError(st, "determinant")
+    return int(d[0])
+
+
+def right_nullspace(A: np.ndarray, p: int) -> np.ndarray:
+    """Basis N (n x (n - r)) of {x : A x = 0}: column c is 1 at the c-th
+    non-pivot column of the RREF (increasing), 0 at the other non-pivot
+    columns, and minus the RREF's entries in that column at the pivot
+    coordinates."""
+    m, n = np.shape(A)
+    E, pc = rref(A, p)
+    r = pc.size
+    free = np.setdiff1d(np.arange(n), pc)
+    N = np.zeros((n, n - r), dtype=np.int64)
+    N[free, np.arange(n - r)] = 1
+    if r:
+        N[pc, :] = (p - E[:r, free].astype(np.int64)) % p
+    return N.astype(np.uint32)
+
+
+def left_nullspace(A: np.ndarray, p: int) -> np.ndarray:
+    """Basis ((m - r) x m) of {y : y A = 0}: the right nullspace of A^T,
+    transposed (identity on the rows outside the row rank profile)."""
+    return np.ascontiguousarray(right_nullspace(np.ascontiguousarray(np.asarray(A).T), p).T)
+
+
+def solve(A: np.ndarray, B: np.ndarray, p: int):
+    """A X = B (A m x n, B m x k).  Returns (X, consistent) where consistent[c]
+    says whether column c has a solution, and X[:, c] is then the solution
+    that is zero at every non-pivot coordinate (RREF of [A | B] with pivots
+    taken in A's columns only)."""
+    A = _u32(A)
+    B = _u32(B)
+    m, n = A.shape
+    k = B.shape[1]
+    E, pc = rref(np.concatenate([A, B], axis=1), p, npiv=n)
+    r = pc.size
+    Bt = E[:, n:]
+    consistent = ~np.any(Bt[r:, :] != 0, axis=0)
+    X = np.zeros((n, k), dtype=np.uint32)
+    X[pc, :] = Bt[:r, :]
+    return X, consistent

@@ -30,6 +30,10 @@
  *   oracle_matmul_sub        MM(C,A,B): C <- C - A B  (Sec. 2 subroutines)
  *   oracle_trsm_*            TRSM(L,B): B <- L^{-1} B, TRSM(B,U): B <- B U^{-1}
  *   oracle_check_pluq        reconstruction A == P [L;M][U V] Q and shape checks
+ *   oracle_rref              reduced row echelon form (Gauss-Jordan); nullspace
+ *                            bases and particular solutions are read off it
+ *                            (uses of the decomposition listed in Sec. 1)
+ *   oracle_determinant       determinant by elimination with row exchanges
  *
  * Readings where the paper is ambiguous (all documented in the design notes):
  *   - base cases m = 1 / n = 1 bring the pivot to the front by a cyclic
@@ -621,4 +625,97 @@ int oracle_check_pluq(const uint32_t *A, int64_t m, int64_t n, int64_t lda, uint
             if (s != A[(int64_t)perm_p[i] * lda + perm_q[j]]) return 6;
         }
     return 0;
+}
+
+/* ------------------------------------------ uses of the decomposition -- */
+/*
+ * The introduction (Sec. 1) lists what a triangular decomposition is used
+ * for: solving linear systems, the rank, the determinant, the nullspace and
+ * the rank profiles.  The oracle computes the first, third and fourth from
+ * their textbook definitions, independently of any PLUQ:
+ *
+ * oracle_rref: reduced row echelon form by Gauss-Jordan elimination, in place
+ * on the m x n block A.  Pivots are searched column by column among the first
+ * npiv columns only (the row operations still act on all n columns, so the
+ * trailing n - npiv columns carry a right-hand side along).  In column c the
+ * first row at or below the current one with a nonzero entry is swapped up,
+ * scaled to a leading one, and column c is cleared in every other row.
+ * piv_col[k] = column of the k-th leading one (increasing).  Returns the
+ * number of pivots, or a negative status.
+ *
+ * The pivot columns of the RREF are the column rank profile (each is the
+ * first column independent of those before it), so the kernel basis whose
+ * restriction to the non-pivot coordinates is the identity, and the solution
+ * whose non-pivot coordinates are zero, are unique and read off the RREF.
+ */
+int64_t oracle_rref(uint32_t *A, int64_t m, int64_t n, int64_t lda, int64_t npiv, uint32_t p,
+                    int32_t *piv_col)
+{
+    int st = validate(A, m, n, lda, p);
+    if (st != O_OK) return st;
+    if (npiv < 0 || npiv > n) return O_EINVAL;
+    int64_t k = 0;
+    for (int64_t c = 0; c < npiv && k < m; ++c) {
+        int64_t s = -1;
+        for (int64_t i = k; i < m; ++i)
+            if (A[i * lda + c] != 0) { s = i; break; }
+        if (s < 0) continue;
+        if (s != k)
+            for (int64_t j = 0; j < n; ++j) {
+                uint32_t t = A[s * lda + j];
+                A[s * lda + j] = A[k * lda + j];
+                A[k * lda + j] = t;
+            }
+        uint32_t inv = inv_mod(A[k * lda + c], p);
+        for (int64_t j = 0; j < n; ++j) A[k * lda + j] = mul_mod(A[k * lda + j], inv, p);
+        for (int64_t i = 0; i < m; ++i) {
+            if (i == k || A[i * lda + c] == 0) continue;
+            uint32_t f = A[i * lda + c];
+            for (int64_t j = 0; j < n; ++j)
+                A[i * lda + j] = sub_mod(A[i * lda + j], mul_mod(f, A[k * lda + j], p), p);
+        }
+        piv_col[k++] = (int32_t)c;
+    }
+    return k;
+}
+
+/*
+ * Determinant of the n x n matrix A by Gaussian elimination with row
+ * exchanges: the product of the pivots, negated once per exchange; zero when
+ * a column has no pivot.  The 0 x 0 determinant is 1.  Returns a status.
+ */
+int oracle_determinant(const uint32_t *A, int64_t n, int64_t lda, uint32_t p, uint32_t *det)
+{
+    int st = validate(A, n, n, lda, p);
+    if (st != O_OK) return st;
+    uint32_t *W = (uint32_t *)malloc((size_t)(n > 0 ? n * n : 1) * sizeof(uint32_t));
+    if (!W) return O_ENOMEM;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) W[i * n + j] = A[i * lda + j];
+    uint32_t d = 1 % p;
+    for (int64_t c = 0; c < n; ++c) {
+        int64_t s = -1;
+        for (int64_t i = c; i < n; ++i)
+            if (W[i * n + c] != 0) { s = i; break; }
+        if (s < 0) { d = 0; break; }
+        if (s != c) {
+            for (int64_t j = 0; j < n; ++j) {
+                uint32_t t = W[s * n + j];
+                W[s * n + j] = W[c * n + j];
+                W[c * n + j] = t;
+            }
+            d = sub_mod(0, d, p);
+        }
+        d = mul_mod(d, W[c * n + c], p);
+        uint32_t inv = inv_mod(W[c * n + c], p);
+        for (int64_t i = c + 1; i < n; ++i) {
+            uint32_t f = mul_mod(W[i * n + c], inv, p);
+            if (f == 0) continue;
+            for (int64_t j = c; j < n; ++j)
+                W[i * n + j] = sub_mod(W[i * n + j], mul_mod(f, W[c * n + j], p), p);
+        }
+    }
+    free(W);
+    *det = d;
+    return O_OK;
 }

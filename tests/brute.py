@@ -98,3 +98,30 @@ def doolittle(A: np.ndarray, p: int):
         for j in range(i + 1, n):
             L[j][i] = ((A[j][i] - sum(L[j][l] * U[l][i] for l in range(i))) * inv) % p
     return np.array(L, dtype=np.int64), np.array(U, dtype=np.int64)
+
+
+def leibniz_det(A, p: int) -> int:
+    """Determinant by the Leibniz formula: the sum over all permutations s of
+    sgn(s) prod_i A[i][s(i)], sgn(s) = (-1)^(number of inversions)."""
+    A = [[int(x) for x in row] for row in np.asarray(A)]
+    n = len(A)
+    total = 0
+    for s in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if s[i] > s[j])
+        term = -1 if inv % 2 else 1
+        for i in range(n):
+            term *= A[i][s[i]]
+        total += term
+    return total % p
+
+
+def permutation_sign(s) -> int:
+    """+1 or -1: (-1)^(number of inversions of the sequence s)."""
+    s = list(s)
+    inv = sum(1 for i in range(len(s)) for j in range(i + 1, len(s)) if s[i] > s[j])
+    return -1 if inv % 2 else 1
+
+
+def all_vectors(n: int, p: int) -> np.ndarray:
+    """Every vector of (Z/pZ)^n, as a (p^n, n) array."""
+    return np.array(list(itertools.product(range(p), repeat=n)), dtype=np.int64).reshape(-1, n)

@@ -400,3 +400,169 @@ def test_descent_free_profiles_are_met_in_row_order():
         A = brute.matmul_mod(brute.matmul_mod(Lc, Rm, 7), Uc, 7).astype(np.uint32)
         _, pp, pq, rr = oracle.pluq_alg1(A, 7)
         assert rr == r and np.array_equal(pp[:r], rows) and np.array_equal(pq[:r], cols)
+
+
+# ------------------------------------------- uses of the decomposition --
+# Sec. 1: linear systems, the determinant and the nullspace.  The oracle
+# computes them from the RREF and from elimination with row exchanges; these
+# pins check them against enumeration, the Leibniz formula and Cramer's rule.
+
+def _profiles_brute(A, p):
+    """(row rank profile, column rank profile) from the brute-force R."""
+    m, n = A.shape
+    if m == 0 or n == 0:
+        return np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64)
+    R = brute.rank_profile_matrix(A, p)[0]
+    rows, cols = np.nonzero(R)
+    return np.sort(rows), np.sort(cols)
+
+
+def _tiny_cases(g, p, shapes, per_shape=6):
+    for m, n in shapes:
+        for t in range(per_shape):
+            r = int(g.integers(0, min(m, n) + 1))
+            if t % 3 == 2:
+                A = g.integers(0, p, (m, n)).astype(np.uint32)
+            else:
+                A, _ = W.planted(m, n, r, p, seed=int(g.integers(1 << 30)))
+            yield A
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7, 65521, 2147483647])
+def test_determinant_matches_leibniz(p):
+    g = np.random.Generator(np.random.PCG64(p + 11))
+    for n in range(0, 7):
+        for t in range(8):
+            if t % 2:
+                A = g.integers(0, p, (n, n)).astype(np.uint32)
+            else:
+                A, _ = W.planted(n, n, int(g.integers(0, n + 1)), p, seed=int(g.integers(1 << 30)))
+            assert oracle.determinant(A, p) == brute.leibniz_det(A, p), (n, t)
+
+
+@pytest.mark.parametrize("n,p", [(40, 65521), (33, 2147483647), (50, 3)])
+def test_determinant_planted_closed_form(n, p):
+    """A = L0 Pi U0 with unit triangular L0, U0: det A = sgn of the planted
+    pairing (rows are 0..n-1, row j has its one in column cols[j])."""
+    A, pl = W.planted(n, n, n, p, seed=n)
+    sgn = brute.permutation_sign(pl.cols)
+    assert oracle.determinant(A, p) == sgn % p
+    B, _ = W.planted(n, n, n - 1, p, seed=n + 1)
+    assert oracle.determinant(B, p) == 0
+
+
+def test_determinant_multiplicative():
+    p = 65521
+    g = np.random.Generator(np.random.PCG64(5))
+    for n in (1, 5, 12):
+        A = g.integers(0, p, (n, n)).astype(np.uint32)
+        B = g.integers(0, p, (n, n)).astype(np.uint32)
+        AB = brute.matmul_mod(A, B, p).astype(np.uint32)
+        assert oracle.determinant(AB, p) == oracle.determinant(A, p) * oracle.determinant(B, p) % p
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_right_nullspace_brute_force(p):
+    """ker A by enumeration equals the span of N's columns, and N is the
+    identity on the coordinates outside the column rank profile."""
+    g = np.random.Generator(np.random.PCG64(100 + p))
+    shapes = [(3, 4), (4, 3), (2, 5), (5, 2), (4, 4), (1, 3)] if p < 5 else [(3, 4), (2, 4), (4, 3)]
+    for A in _tiny_cases(g, p, shapes):
+        m, n = A.shape
+        N = oracle.right_nullspace(A, p).astype(np.int64)
+        _, cols = _profiles_brute(A, p)
+        r = cols.size
+        assert N.shape == (n, n - r)
+        free = np.setdiff1d(np.arange(n), cols)
+        assert np.array_equal(N[free, :], np.eye(n - r, dtype=np.int64))
+        X = brute.all_vectors(n, p)
+        ker = {tuple(x) for x in X if not np.any(brute.matmul_mod(A, x[:, None], p))}
+        Y = brute.all_vectors(n - r, p) if n > r else np.zeros((1, 0), dtype=np.int64)
+        span = {tuple(v) for v in (brute.matmul_mod(N, Y.T, p).T if n > r else
+                                   np.zeros((1, n), dtype=np.int64))}
+        assert ker == span
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_left_nullspace_brute_force(p):
+    """{y : y A = 0} by enumeration equals the row span of the left basis,
+    which is the identity on the rows outside the row rank profile."""
+    g = np.random.Generator(np.random.PCG64(200 + p))
+    for A in _tiny_cases(g, p, [(4, 3), (3, 4), (5, 2), (2, 2)]):
+        m, n = A.shape
+        N = oracle.left_nullspace(A, p).astype(np.int64)
+        rows, _ = _profiles_brute(A, p)
+        r = rows.size
+        assert N.shape == (m - r, m)
+        free = np.setdiff1d(np.arange(m), rows)
+        assert np.array_equal(N[:, free], np.eye(m - r, dtype=np.int64))
+        Y = brute.all_vectors(m, p)
+        ker = {tuple(y) for y in Y if not np.any(brute.matmul_mod(y[None, :], A, p))}
+        Z = brute.all_vectors(m - r, p) if m > r else np.zeros((1, 0), dtype=np.int64)
+        span = {tuple(v) for v in (brute.matmul_mod(Z, N, p) if m > r else
+                                   np.zeros((1, m), dtype=np.int64))}
+        assert ker == span
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_solve_brute_force(p):
+    """Per right-hand side: consistent iff enumeration finds a solution, and
+    the returned one is the only solution that vanishes outside the column
+    rank profile."""
+    g = np.random.Generator(np.random.PCG64(300 + p))
+    for A in _tiny_cases(g, p, [(3, 4), (4, 3), (4, 4), (2, 5)] if p < 5 else [(3, 4), (4, 3)]):
+        m, n = A.shape
+        k = 4
+        B = g.integers(0, p, (m, k)).astype(np.uint32)
+        B[:, 0] = brute.matmul_mod(A, g.integers(0, p, (n, 1)), p)[:, 0]   # one consistent column
+        X, ok = oracle.solve(A, B, p)
+        _, cols = _profiles_brute(A, p)
+        free = np.setdiff1d(np.arange(n), cols)
+        V = brute.all_vectors(n, p)
+        AV = brute.matmul_mod(A, V.T, p).T                                 # (p^n, m)
+        for c in range(k):
+            sols = V[np.all(AV == B[:, c].astype(np.int64)[None, :], axis=1)]
+            assert bool(ok[c]) == (len(sols) > 0)
+            if len(sols):
+                canon = sols[np.all(sols[:, free] == 0, axis=1)]
+                assert len(canon) == 1
+                assert np.array_equal(X[:, c].astype(np.int64), canon[0])
+        assert ok[0]
+
+
+def test_solve_cramer():
+    """Nonsingular A: x_i = det(A with column i replaced by b) / det(A)."""
+    p = 65521
+    g = np.random.Generator(np.random.PCG64(9))
+    for n in (1, 3, 5):
+        A, _ = W.planted(n, n, n, p, seed=n + 50)
+        b = g.integers(0, p, (n, 1)).astype(np.uint32)
+        X, ok = oracle.solve(A, b, p)
+        assert ok.all()
+        d = brute.leibniz_det(A, p)
+        dinv = pow(d, p - 2, p)
+        for i in range(n):
+            Ai = A.copy()
+            Ai[:, i] = b[:, 0]
+            assert int(X[i, 0]) == brute.leibniz_det(Ai, p) * dinv % p
+
+
+def test_nullspace_and_solve_medium():
+    """At 60 x 80: A N = 0, N A' = 0, A X = B on the consistent columns, with
+    exact Python-integer products."""
+    p = 8388593
+    A, pl = W.planted(60, 80, 37, p, seed=3)
+    N = oracle.right_nullspace(A, p)
+    assert N.shape == (80, 43)
+    assert not np.any(brute.matmul_mod(A, N, p))
+    Nl = oracle.left_nullspace(A, p)
+    assert Nl.shape == (23, 60)
+    assert not np.any(brute.matmul_mod(Nl, A, p))
+    g = np.random.Generator(np.random.PCG64(4))
+    B = brute.matmul_mod(A, g.integers(0, p, (80, 3)), p).astype(np.uint32)
+    X, ok = oracle.solve(A, B, p)
+    assert ok.all()
+    assert np.array_equal(brute.matmul_mod(A, X, p), B.astype(np.int64))
+    B2 = g.integers(0, p, (60, 2)).astype(np.uint32)
+    _, ok2 = oracle.solve(A, B2, p)
+    assert not ok2.any()                 # random right-hand sides miss a rank-37 image
