@@ -175,6 +175,71 @@ pluq_status pluq_leading_rank_profiles(const int32_t *d_perm_p, const int32_t *d
                                        void *stream);
 
 /*
+ * Uses of the decomposition (Sec. 1 names linear systems, the determinant
+ * and the nullspace among them), read off the packed result of pluq_mod_p:
+ * d_LU (m x n, stride lda >= n, not modified), its rank r and its d_perm_p /
+ * d_perm_q, which must be the permutations pluq_mod_p returned (entries are
+ * used as indices).  Because the pivot columns (rows) are the column (row)
+ * rank profile, every result below is unique, not just a valid choice.
+ * All are asynchronous on `stream`; products run on the kernel form mm_kind.
+ * Scratch: d_work of at least pluq_uses_workspace_size(m, n, r, k, p,
+ * mm_kind) bytes covers each of these calls for those sizes (k = number of
+ * right-hand sides of pluq_solve, 0 otherwise).  Errors: EINVAL (sizes,
+ * strides, null pointers), ENOTPRIME, ENOMEM (workspace), ECUDA.
+ */
+pluq_status pluq_uses_workspace_size(int64_t m, int64_t n, int64_t r, int64_t k, uint32_t p,
+                                     int mm_kind, size_t *h_bytes);
+
+/*
+ * Determinant of a square A (n x n): 0 when r < n, else
+ * sgn(P) sgn(Q) prod_i U[i][i] mod p, the signs from the cycle counts of
+ * perm_p and perm_q.  The 0 x 0 determinant is 1.  d_det: one device uint32.
+ */
+pluq_status pluq_determinant(const uint32_t *d_LU, int64_t n, int64_t lda, int64_t r,
+                             const int32_t *d_perm_p, const int32_t *d_perm_q, uint32_t p,
+                             uint32_t *d_det, void *d_work, size_t ws_bytes, void *stream);
+
+/*
+ * Right nullspace: d_N (n x (n - r), stride ldn >= n - r) receives
+ * N = Q^T [-U^{-1} V; I_{n-r}], so A N = 0 and column c of N is the unit
+ * vector on the c-th column outside the column rank profile (increasing)
+ * plus the combination of rank-profile columns that cancels it.  Nothing is
+ * written when r = n.
+ */
+pluq_status pluq_right_nullspace(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda,
+                                 int64_t r, const int32_t *d_perm_q, uint32_t p, uint32_t *d_N,
+                                 int64_t ldn, int mm_kind, void *d_work, size_t ws_bytes,
+                                 void *stream);
+
+/*
+ * Left nullspace: d_K ((m - r) x m, stride ldk >= m) receives
+ * K = [-M L^{-1}, I_{m-r}] P^T, so K A = 0 and row c of K is the unit vector
+ * on the c-th row outside the row rank profile (increasing) plus the
+ * combination of rank-profile rows that cancels it.  Nothing is written when
+ * r = m.
+ */
+pluq_status pluq_left_nullspace(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda,
+                                int64_t r, const int32_t *d_perm_p, uint32_t p, uint32_t *d_K,
+                                int64_t ldk, int mm_kind, void *d_work, size_t ws_bytes,
+                                void *stream);
+
+/*
+ * A X = B for k right-hand sides: d_B (m x k, stride ldb >= k, entries in
+ * [0, p), not range-checked: an entry >= p gives unspecified values but no
+ * out-of-bounds access), d_X (n x k, stride ldx >= k, must not overlap d_B).
+ * With Y = [L 0; M I]^{-1} P^T B, column c is solvable iff Y[r:, c] = 0;
+ * *d_inconsistent (device int32) is set to 0 if every column is, else 1.
+ * d_X receives Q^T [U^{-1} Y[:r, :]; 0]: for every solvable column, the
+ * solution that is zero outside the column rank profile (for a nonsingular A,
+ * the solution).
+ */
+pluq_status pluq_solve(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                       const int32_t *d_perm_p, const int32_t *d_perm_q, uint32_t p,
+                       const uint32_t *d_B, int64_t ldb, int64_t k, uint32_t *d_X, int64_t ldx,
+                       int32_t *d_inconsistent, int mm_kind, void *d_work, size_t ws_bytes,
+                       void *stream);
+
+/*
  * Hot-path kernels of Algorithm 1, callable on their own.
  *
  * MM(C, A, B) of Sec. 2: C <- C - A B mod p (or C <- A B mod p when `assign`

@@ -154,33 +154,36 @@ __global__ void extract_kernel(const uint32_t *__restrict__ LU, int64_t lda, int
         }
 }
 
-// inv[perm[i]] = i
+// inv[perm[i]] = i (entries of perm outside [0, n) are skipped)
 __global__ void inverse_perm_kernel(const int32_t *__restrict__ perm, int64_t n,
                                     int32_t *__restrict__ inv)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) inv[perm[i]] = (int32_t)i;
+    if (i >= n) return;
+    const int64_t v = (uint32_t)perm[i];
+    if (v < n) inv[v] = (int32_t)i;
 }
 
 // LEU read-out (Corollary of the triangularity theorem, Sec. 3), in original
 // row / column indices.  lower: Lbar (m x m) = P [L 0; M I] P^T, entry (a, b)
 // taken at packed position (inv[a], inv[b]); otherwise Ubar (n x n) =
-// Q^T [U V; 0 0] Q, likewise.
+// Q^T [U V; 0 0] Q, likewise.  LU is read only at positions inside the block,
+// whatever inv holds.
 __global__ void leu_kernel(const uint32_t *__restrict__ LU, int64_t lda, int64_t dim, int64_t r,
                            const int32_t *__restrict__ inv, uint32_t *__restrict__ X, int64_t ldx,
                            int lower)
 {
     const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
     for (int64_t a = blockIdx.y; a < dim; a += gridDim.y) {
-        const int64_t i = inv[a];
+        const int64_t i = (uint32_t)inv[a];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int64_t b = c0 + (int64_t)s * GT;
             if (b >= dim) continue;
-            const int64_t j = inv[b];
+            const int64_t j = (uint32_t)inv[b];
             uint32_t v;
-            if (lower) v = i == j ? 1u : ((j < r && i > j) ? LU[i * lda + j] : 0u);
-            else v = (i < r && j >= i) ? LU[i * lda + j] : 0u;
+            if (lower) v = i == j ? 1u : ((j < r && i > j && i < dim) ? LU[i * lda + j] : 0u);
+            else v = (i < r && j >= i && j < dim) ? LU[i * lda + j] : 0u;
             X[a * ldx + b] = v;
         }
     }

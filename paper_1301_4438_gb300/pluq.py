@@ -45,6 +45,17 @@ _SIGS = {
                                 _c_i64, _vp, ctypes.c_size_t, _vp]),
     "pluq_leading_rank_profiles": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _c_i64,
                                                   _vp, _vp, _vp, _vp]),
+    "pluq_uses_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _c_i64, _c_u32,
+                                                ctypes.c_int, _szp]),
+    "pluq_determinant": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _vp, _vp, _c_u32, _vp, _vp,
+                                        ctypes.c_size_t, _vp]),
+    "pluq_right_nullspace": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _c_u32, _vp,
+                                            _c_i64, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "pluq_left_nullspace": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _c_u32, _vp,
+                                           _c_i64, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "pluq_solve": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp, _c_u32, _vp,
+                                  _c_i64, _c_i64, _vp, _c_i64, _vp, ctypes.c_int, _vp,
+                                  ctypes.c_size_t, _vp]),
     "pluq_modmm_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _c_u32, ctypes.c_int,
                                                  _szp]),
     "pluq_modmm": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _c_i64, _c_i64, _c_i64,
@@ -245,6 +256,88 @@ def pluq_leading_rank_profiles(perm_p: torch.Tensor, perm_q: torch.Tensor, r: in
            "pluq_leading_rank_profiles")
     c = int(count.item())
     return rows[:c], cols[:c]
+
+
+def uses_workspace_size(m: int, n: int, r: int, k: int, p: int, mm: str = "auto") -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().pluq_uses_workspace_size(m, n, r, k, p, _KIND[mm], ctypes.byref(out)),
+           "pluq_uses_workspace_size")
+    return int(out.value)
+
+
+def _uses_ws(m, n, r, k, p, mm, workspace, dev):
+    need = uses_workspace_size(m, n, r, k, p, mm)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    return workspace
+
+
+def _ld(X: torch.Tensor, cols: int) -> int:
+    return X.stride(0) if X.shape[0] > 0 else max(cols, 1)
+
+
+def pluq_determinant(LU: torch.Tensor, perm_p: torch.Tensor, perm_q: torch.Tensor, r: int,
+                     p: int, workspace=None, stream=None) -> torch.Tensor:
+    """det A mod p (A square) from its PLUQ, as a one-element device tensor
+    (int32 holding the uint32 value)."""
+    _need_cuda(LU, perm_p, perm_q)
+    n, n2 = LU.shape
+    if n != n2:
+        raise ValueError("the determinant needs a square matrix")
+    det = torch.zeros(1, dtype=torch.int32, device=LU.device)
+    ws = _uses_ws(n, n, r, 0, p, "auto", workspace, LU.device)
+    _check(load().pluq_determinant(_ptr(LU), n, _ld(LU, n), r, _ptr(perm_p), _ptr(perm_q), p,
+                                   _ptr(det), _ptr(ws), ws.numel(), _stream(stream)),
+           "pluq_determinant")
+    return det
+
+
+def pluq_right_nullspace(LU: torch.Tensor, perm_q: torch.Tensor, r: int, p: int,
+                         mm: str = "auto", workspace=None, stream=None) -> torch.Tensor:
+    """N (n x (n - r)) with A N = 0: Q^T [-U^{-1} V; I]."""
+    _need_cuda(LU, perm_q)
+    m, n = LU.shape
+    N = torch.empty((n, n - r), dtype=LU.dtype, device=LU.device)
+    ws = _uses_ws(m, n, r, 0, p, mm, workspace, LU.device)
+    _check(load().pluq_right_nullspace(_ptr(LU), m, n, _ld(LU, n), r, _ptr(perm_q), p, _ptr(N),
+                                       max(n - r, 1), _KIND[mm], _ptr(ws), ws.numel(),
+                                       _stream(stream)), "pluq_right_nullspace")
+    return N
+
+
+def pluq_left_nullspace(LU: torch.Tensor, perm_p: torch.Tensor, r: int, p: int,
+                        mm: str = "auto", workspace=None, stream=None) -> torch.Tensor:
+    """K ((m - r) x m) with K A = 0: [-M L^{-1}, I] P^T."""
+    _need_cuda(LU, perm_p)
+    m, n = LU.shape
+    K = torch.empty((m - r, m), dtype=LU.dtype, device=LU.device)
+    ws = _uses_ws(m, n, r, 0, p, mm, workspace, LU.device)
+    _check(load().pluq_left_nullspace(_ptr(LU), m, n, _ld(LU, n), r, _ptr(perm_p), p, _ptr(K),
+                                      max(m, 1), _KIND[mm], _ptr(ws), ws.numel(),
+                                      _stream(stream)), "pluq_left_nullspace")
+    return K
+
+
+def pluq_solve(LU: torch.Tensor, perm_p: torch.Tensor, perm_q: torch.Tensor, r: int,
+               B: torch.Tensor, p: int, mm: str = "auto", workspace=None, stream=None):
+    """A X = B (B m x k, rows contiguous).  Returns (X n x k, inconsistent):
+    inconsistent is a one-element device tensor, 1 if some column of B has no
+    solution; X holds, per solvable column, the solution that is zero outside
+    the column rank profile."""
+    _need_cuda(LU, perm_p, perm_q, B)
+    m, n = LU.shape
+    if B.dim() != 2 or B.shape[0] != m:
+        raise ValueError("B must be m x k")
+    if B.numel() and B.stride(1) != 1:
+        raise ValueError("rows of B must be contiguous")
+    k = B.shape[1]
+    X = torch.empty((n, k), dtype=LU.dtype, device=LU.device)
+    flag = torch.empty(1, dtype=torch.int32, device=LU.device)
+    ws = _uses_ws(m, n, r, k, p, mm, workspace, LU.device)
+    _check(load().pluq_solve(_ptr(LU), m, n, _ld(LU, n), r, _ptr(perm_p), _ptr(perm_q), p,
+                             _ptr(B), _ld(B, k), k, _ptr(X), max(k, 1), _ptr(flag), _KIND[mm],
+                             _ptr(ws), ws.numel(), _stream(stream)), "pluq_solve")
+    return X, flag
 
 
 def modmm_workspace_size(M: int, N: int, K: int, p: int, mm: str = "auto") -> int:
