@@ -47,11 +47,14 @@ def parse():
     ap.add_argument("--workload", default="dense_4096")
     ap.add_argument("--mm", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["pluq", "gemm", "leaf"], default=None,
+    ap.add_argument("--profile", choices=["pluq", "gemm", "leaf", "trsm"], default=None,
                     help="untimed: one warm-up and one decomposition of the workload (pluq), one "
-                         "modular product of --shape M,N,K (gemm), or one base-case call on a "
-                         "uniform --shape M,N block (leaf), for external profilers")
-    ap.add_argument("--shape", default="8192,8192,2048", help="sizes for --profile gemm / leaf")
+                         "modular product of --shape M,N,K (gemm), one base-case call on a "
+                         "uniform --shape M,N block (leaf), or the left and right triangular "
+                         "solves with an r x r triangle and N right-hand sides, --shape r,N "
+                         "(trsm), each twice, for external profilers")
+    ap.add_argument("--shape", default="8192,8192,2048",
+                    help="sizes for --profile gemm / leaf / trsm")
     ap.add_argument("--p", type=int, default=65521, help="modulus for --profile gemm")
     return ap.parse_args()
 
@@ -64,6 +67,15 @@ def run_profile_target(args):
         A0 = torch.from_numpy(W.uniform(m, n, args.p, W.BASE_SEED + 5).astype(np.int32)).cuda()
         for _ in range(2):
             pluq.pluq_leaf(A0.clone(), args.p)
+    elif args.profile == "trsm":
+        r, N = (int(x) for x in args.shape.split(",")[:2])
+        g = np.random.Generator(np.random.PCG64(W.BASE_SEED + 6))
+        T = torch.from_numpy(g.integers(1, args.p, (r, r)).astype(np.int32)).cuda()
+        B = torch.from_numpy(g.integers(0, args.p, (r, N)).astype(np.int32)).cuda()
+        Bt = torch.from_numpy(g.integers(0, args.p, (N, r)).astype(np.int32)).cuda()
+        for _ in range(2):
+            pluq.pluq_trsm_left_lower_unit(T, B.clone(), args.p, mm=args.mm)
+            pluq.pluq_trsm_right_upper(T, Bt.clone(), args.p, mm=args.mm)
     elif args.profile == "gemm":
         M, N, K = (int(x) for x in args.shape.split(","))
         p = args.p

@@ -387,10 +387,17 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
     const uint32_t p = F.p;
     const uint32_t w16 = (uint32_t)((1ull << 16) % p);
     uint32_t *W = S.W;
+    // asynchronous 4-byte copies: the whole block is in flight at once
     for (int i = warp; i < m; i += NW) {
         const int64_t src = rowmap ? rowmap[i] : i;
-        for (int j = lane; j < n; j += 32) W[i * LD + j] = A[src * lda + (colmap ? colmap[j] : j)];
+        for (int j = lane; j < n; j += 32) {
+            const unsigned dst = smem_addr(&W[i * LD + j]);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst),
+                         "l"(&A[src * lda + (colmap ? colmap[j] : j)])
+                         : "memory");
+        }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     if (tid == 0) S.gfail = 0;
     __syncthreads();
     const int kmax = kcap >= 0 ? kcap : (m < n ? m : n);

@@ -1,87 +1,109 @@
 // TRSM of Sec. 2 on the GPU:  B <- L^{-1} B (L unit lower) and B <- B U^{-1}
 // (U upper, nonzero diagonal).
 //
-// Instead of a substitution whose critical path is one column of B per step,
-// the triangle is inverted first and the solve becomes one modular product:
-//   - 32 x 32 diagonal blocks are inverted by substitution, one thread block
-//     per diagonal block, all blocks in one launch;
-//   - blocks are then merged pairwise, log2(r/32) levels, with
-//       [L11 0; L21 L22]^-1 = [X11 0; -X22 L21 X11  X22],
-//       [U11 U12; 0 U22]^-1 = [X11 -X11 U12 X22; 0 X22],
-//     every pair of a level in one batched product launch;
-//   - the solve is X B (or B X).
-// The inverse costs r^3/3 field operations, small next to the r^2 N of the
-// solve for the shapes Algorithm 1 produces, and the launches per TRSM drop
-// from O(r/32) to O(log(r/32)).  Triangles of at most 64 rows are solved
-// directly by substitution instead (one launch).
+// Triangles of at most WR = 128 rows are solved directly, in one launch, by
+// blocks of BS = 32: every thread block inverts the (at most four) 32 x 32
+// diagonal blocks of the triangle, then for k = 0, 1, ... computes, for its
+// 32 right-hand sides,
+//   left:  Y = B_k - L_{k,<k} X_{<k},   X_k = L_kk^{-1} Y
+//   right: Y = B_k - X_{<k} U_{<k,k},   X_k = Y U_kk^{-1}.
+// The substitution chain is thus 32 rows long (inside the diagonal inverses,
+// shared by all right-hand sides) instead of r, and the rest is dot products
+// on shared memory with delayed reduction.
+//
+// Larger triangles are inverted first and the solve becomes one modular
+// product: the 128 x 128 diagonal blocks are inverted by the direct solver
+// with the identity as right-hand side (all blocks in one launch), then merged
+// pairwise, log2(r/128) levels, with
+//     [L11 0; L21 L22]^-1 = [X11 0; -X22 L21 X11  X22],
+//     [U11 U12; 0 U22]^-1 = [X11 -X11 U12 X22; 0 X22],
+// every pair of a level in one batched product launch; the solve is X B (or
+// B X).  The inverse costs r^3/3 field operations, small next to the r^2 N of
+// the solve for the shapes Algorithm 1 produces.
 #include "common.cuh"
 
 namespace pluq {
 namespace {
 
+constexpr int WR = 128;            // largest triangle solved directly
+constexpr int BS = 32;             // diagonal block of the direct solver
+constexpr int NBLK = WR / BS;      // diagonal blocks of the largest triangle
+constexpr int NRHS = 32;           // right-hand sides per thread block
+constexpr int TT = 256;            // threads per block
+constexpr int NWARP = TT / 32;     // warps per block
+constexpr int RPW = BS / NWARP;    // rows (left) or right-hand sides (right) per warp
+constexpr int TB = WR;             // diagonal blocks the inverses start from
 
-// Sum of up to 2^17 products a_l * b_l (a, b < 2^31) held exactly in 64-bit
-// words.  p <= 2^16: one word (products < 2^32).  Otherwise a = a_hi 2^16 +
-// a_lo and two words; w16 = 2^16 mod p recombines them.
+// Dot product sum_l a_l b_l of residues (a, b < p), exact until read.
+// p <= 2^16: one 64-bit word (each product < 2^32).  Otherwise b is split as
+// b_hi 2^16 + b_lo into two words (products < 2^47, so up to 2^17 terms) and
+// w16 = 2^16 mod p recombines them.  Callers pass the operand shared by
+// several sums as b, so its split is computed once.
 template <bool SMALLP>
-struct Acc {
+struct Dot;
+
+template <>
+struct Dot<true> {
+    uint64_t s = 0;
+    __device__ __forceinline__ void add(uint32_t a, uint32_t b) { s += (uint64_t)a * b; }
+    __device__ __forceinline__ uint32_t value(const Field &F, uint32_t) const
+    {
+        return reduce64(s, F);
+    }
+};
+
+template <>
+struct Dot<false> {
     uint64_t lo = 0, hi = 0;
     __device__ __forceinline__ void add(uint32_t a, uint32_t b)
     {
-        if (SMALLP) {
-            lo += (uint64_t)(a * b);
-        } else {
-            lo += (uint64_t)(a & 0xFFFFu) * b;
-            hi += (uint64_t)(a >> 16) * b;
-        }
+        lo += (uint64_t)a * (b & 0xFFFFu);
+        hi += (uint64_t)a * (b >> 16);
     }
     __device__ __forceinline__ uint32_t value(const Field &F, uint32_t w16) const
     {
-        if (SMALLP) return reduce64(lo, F);
         return add_mod(reduce64(lo, F), mul_mod(reduce64(hi, F), w16, F), F.p);
     }
 };
 
-// Direct solves for narrow triangles (r <= WR): one warp per right-hand side
-// (a column of B for the left solve, a row of B for the right one), lane q
-// owning triangle rows / columns q, q + 32, ...  The unknowns are produced one
-// per step: the owner of the next unknown finishes it and broadcasts it with a
-// shuffle, every lane adds its term into the running sums of its later rows.
-// The owner's sum over the earlier terms is reduced one step ahead, so a step's
-// dependency chain is one shuffle, one modular product and two subtractions.
-constexpr int WR = 128, WT = 256, WPB = WT / 32;
-constexpr int TB = WR;   // diagonal blocks the inverses start from
-
-template <bool SMALLP>
-__device__ __forceinline__ uint32_t prod_mod(uint32_t a, uint32_t b, const Field &F,
-                                             const Field32 &F32)
+// 4-byte asynchronous global -> shared copy: every element of a staged
+// triangle is in flight at once instead of one row's latency after another.
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src)
 {
-    if (SMALLP) return reduce32(a * b, F32);
-    return mul_mod(a, b, F);
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
 }
 
-template <int RPL, typename T>
-__device__ __forceinline__ T slot_pick(const T (&v)[RPL], int s)
+__device__ __forceinline__ void cp_async_wait_all()
 {
-    T x = v[0];
-#pragma unroll
-    for (int t = 1; t < RPL; ++t)
-        if (s == t) x = v[t];
-    return x;
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// odd row stride of the staged triangle: a lane per row reads without conflicts
-__host__ __device__ __forceinline__ int tri_ld(int r) { return (r & 1) ? r + 2 : r + 1; }
+// Shared memory of the direct solvers (32-bit words).  Strides are those of
+// the largest triangle, so nothing depends on r; rows or columns at or past r
+// are never staged and every value read from them is multiplied by zero or
+// discarded.
+constexpr size_t SM_TRI = (size_t)WR * WR;            // the triangle, row stride WR
+constexpr size_t SM_INV = (size_t)NBLK * BS * BS;     // inverses of the diagonal blocks
+constexpr size_t SM_X = (size_t)WR * NRHS;            // right-hand sides / unknowns
+constexpr size_t SM_Y = (size_t)BS * NRHS;            // Y of the current block
+constexpr size_t SM_LEFT = (SM_TRI + SM_INV + SM_X + SM_Y) * 4;
+constexpr size_t SM_RIGHT = (SM_TRI + SM_INV + SM_X + SM_Y + WR) * 4;
 
-// B (r x N) <- L^{-1} B, L unit lower (diagonal not read).  IDENT: blockIdx.y
-// picks the diagonal block of L at o = blockIdx.y * blk (size min(blk, r - o))
-// and B receives its inverse there (the right-hand side is the identity).
-template <bool SMALLP, int RPL, bool IDENT>
-__global__ void __launch_bounds__(WT) trsm_left_warp(const uint32_t *__restrict__ L, int64_t ldl,
-                                                      uint32_t *__restrict__ B, int64_t ldb, int r,
-                                                      int64_t N, Field F, int blk)
+// B (r x N) <- L^{-1} B, L unit lower (diagonal not read); thread block x
+// takes columns [32 x, 32 x + 32) of B.  IDENT: blockIdx.y picks the diagonal
+// block of L at o = blockIdx.y * blk (size min(blk, r - o)) and B receives its
+// inverse there (the right-hand side is the identity).
+template <bool SMALLP, bool IDENT>
+__global__ void __launch_bounds__(TT) trsm_left_blocked(const uint32_t *__restrict__ L, int64_t ldl,
+                                                         uint32_t *__restrict__ B, int64_t ldb,
+                                                         int r, int64_t N, Field F, int blk)
 {
-    extern __shared__ uint32_t Ls[];
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *Ls = sm;                  // [WR][WR]
+    uint32_t *Li = Ls + SM_TRI;         // [NBLK][BS][BS]
+    uint32_t *Xs = Li + SM_INV;         // [WR][NRHS]
+    uint32_t *Ys = Xs + SM_X;           // [BS][NRHS]
     if (IDENT) {
         const int64_t o = (int64_t)blockIdx.y * blk;
         L += o * (ldl + 1);
@@ -89,61 +111,86 @@ __global__ void __launch_bounds__(WT) trsm_left_warp(const uint32_t *__restrict_
         r = min(blk, (int)(r - o));
         N = r;
     }
-    const int ld = tri_ld(r);
-    {
-        const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        for (int i = w; i < r; i += nw)
-#pragma unroll 4
-            for (int c = l; c < i; c += 32) Ls[i * ld + c] = L[(int64_t)i * ldl + c];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * NRHS + lane;    // this lane's column of B
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    for (int i = warp; i < r; i += NWARP) {
+        for (int c = lane; c < i; c += 32) cp_async4(&Ls[i * WR + c], &L[(int64_t)i * ldl + c]);
+        if (IDENT) Xs[i * NRHS + lane] = i == j ? 1u : 0u;
+        else if (j < N) cp_async4(&Xs[i * NRHS + lane], &B[(int64_t)i * ldb + j]);
+        else Xs[i * NRHS + lane] = 0u;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // inverse of diagonal block `warp`: lane c computes its column c,
+    // x_c = 1, x_i = -sum_{c <= l < i} L_il x_l (i > c), zero above
+    const int nblk = (r + BS - 1) / BS;
+    if (warp < nblk) {
+        const int b0 = warp * BS;
+        uint32_t x[BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            Dot<SMALLP> acc;
+#pragma unroll
+            for (int l = 0; l < i; ++l) acc.add(Ls[(b0 + i) * WR + b0 + l], x[l]);
+            const uint32_t v = sub_mod(0u, acc.value(F, w16), F.p);
+            x[i] = (i < lane || b0 + i >= r) ? 0u : (i == lane ? 1u : v);
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i) Li[(b0 + i) * BS + lane] = x[i];
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *xs = Ls + r * ld + warp * WR;            // this warp's unknowns
-    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (j >= N) return;
-    const Field32 F32{F.p, 0xFFFFFFFFu / F.p};
-    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    uint32_t b[RPL];
-    Acc<SMALLP> acc[RPL];
+
+    for (int k = 0; k < nblk; ++k) {
+        const int b0 = k * BS;
+        // Y = B_k - L_{k,<k} X_{<k}: rows b0 + warp + NWARP q, column lane
+        Dot<SMALLP> acc[RPW];
+        for (int l = 0; l < b0; ++l) {
+            const uint32_t xv = Xs[l * NRHS + lane];
 #pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-        const int row = lane + 32 * t;
-        if (IDENT) b[t] = row == j ? 1u : 0u;
-        else b[t] = row < r ? B[(int64_t)row * ldb + j] : 0u;
-    }
-    uint32_t x = __shfl_sync(0xFFFFFFFFu, b[0], 0);   // x_0 = b_0
-    if (lane == 0) xs[0] = x;
-    uint32_t vnext = 0;                               // owner's sum for row i + 1, terms < i
-    for (int i = 0; i + 1 < r; ++i) {
-        const int nr = i + 1, nl = nr & 31, ns = nr >> 5;
-        const uint32_t lx = Ls[nr * ld + i];
-        const uint32_t xn = sub_mod(sub_mod(slot_pick<RPL>(b, ns), vnext, F.p),
-                                    prod_mod<SMALLP>(lx, x, F, F32), F.p);
-#pragma unroll
-        for (int t = 0; t < RPL; ++t) {
-            const int row = lane + 32 * t;
-            if (row > nr && row < r) acc[t].add(Ls[row * ld + i], x);
+            for (int q = 0; q < RPW; ++q) acc[q].add(Ls[(b0 + warp + NWARP * q) * WR + l], xv);
         }
-        x = __shfl_sync(0xFFFFFFFFu, xn, nl);
-        if (lane == 0) xs[nr] = x;
-        vnext = slot_pick<RPL>(acc, (i + 2) >> 5).value(F, w16);
-    }
-    __syncwarp();
 #pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-        const int row = lane + 32 * t;
-        if (row < r) B[(int64_t)row * ldb + j] = xs[row];
+        for (int q = 0; q < RPW; ++q) {
+            const int i = warp + NWARP * q;
+            Ys[i * NRHS + lane] = sub_mod(Xs[(b0 + i) * NRHS + lane], acc[q].value(F, w16), F.p);
+        }
+        __syncthreads();
+        // X_k = L_kk^{-1} Y (the inverse is zero above its diagonal and in
+        // the rows and columns past r, so the full 32-term sums are exact)
+        Dot<SMALLP> acc2[RPW];
+#pragma unroll 8
+        for (int l = 0; l < BS; ++l) {
+            const uint32_t yv = Ys[l * NRHS + lane];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) acc2[q].add(Li[(b0 + warp + NWARP * q) * BS + l], yv);
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int i = b0 + warp + NWARP * q;
+            if (i < r) Xs[i * NRHS + lane] = acc2[q].value(F, w16);
+        }
+        __syncthreads();
     }
+    if (j < N)
+        for (int i = warp; i < r; i += NWARP) B[(int64_t)i * ldb + j] = Xs[i * NRHS + lane];
 }
 
-// B (M x r) <- B U^{-1}, U upper with nonzero diagonal.  IDENT: as for the
-// left solve, B receives the inverse of the diagonal block blockIdx.y of U.
-template <bool SMALLP, int RPL, bool IDENT>
-__global__ void __launch_bounds__(WT) trsm_right_warp(const uint32_t *__restrict__ U, int64_t ldu,
-                                                       uint32_t *__restrict__ B, int64_t ldb,
-                                                       int64_t M, int r, Field F, int blk)
+// B (M x r) <- B U^{-1}, U upper with nonzero diagonal; thread block x takes
+// rows [32 x, 32 x + 32) of B.  IDENT: as for the left solve, B receives the
+// inverse of the diagonal block blockIdx.y of U.
+template <bool SMALLP, bool IDENT>
+__global__ void __launch_bounds__(TT) trsm_right_blocked(const uint32_t *__restrict__ U, int64_t ldu,
+                                                          uint32_t *__restrict__ B, int64_t ldb,
+                                                          int64_t M, int r, Field F, int blk)
 {
-    extern __shared__ uint32_t Us[];
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *Us = sm;                  // [WR][WR]
+    uint32_t *Ui = Us + SM_TRI;         // [NBLK][BS][BS]
+    uint32_t *Xs = Ui + SM_INV;         // [NRHS][WR]
+    uint32_t *Ys = Xs + SM_X;           // [NRHS][BS]
+    uint32_t *dinv = Ys + SM_Y;         // [WR]
     if (IDENT) {
         const int64_t o = (int64_t)blockIdx.y * blk;
         U += o * (ldu + 1);
@@ -151,92 +198,112 @@ __global__ void __launch_bounds__(WT) trsm_right_warp(const uint32_t *__restrict
         r = min(blk, (int)(r - o));
         M = r;
     }
-    const int ld = tri_ld(r);
-    uint32_t *dinv = Us + r * ld;
-    {
-        const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        for (int i = w; i < r; i += nw)
-#pragma unroll 4
-            for (int c = i + l; c < r; c += 32) Us[i * ld + c] = U[(int64_t)i * ldu + c];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < r; t += blockDim.x) dinv[t] = inv_mod(Us[t * ld + t], F.p);
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *xs = dinv + WR + warp * WR;              // this warp's unknowns
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (i >= M) return;
-    const Field32 F32{F.p, 0xFFFFFFFFu / F.p};
+    const int64_t m0 = (int64_t)blockIdx.x * NRHS;
     const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    uint32_t b[RPL];
-    Acc<SMALLP> acc[RPL];
-#pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-        const int c = lane + 32 * t;
-        if (IDENT) b[t] = c == i ? 1u : 0u;
-        else b[t] = c < r ? B[i * ldb + c] : 0u;
-    }
-    uint32_t x = prod_mod<SMALLP>(__shfl_sync(0xFFFFFFFFu, b[0], 0), dinv[0], F, F32);
-    if (lane == 0) xs[0] = x;
-    uint32_t vnext = 0;
-    for (int l = 0; l + 1 < r; ++l) {
-        const int nc = l + 1, nl = nc & 31, ns = nc >> 5;
-        const uint32_t ux = Us[l * ld + nc];
-        const uint32_t xn = prod_mod<SMALLP>(
-            sub_mod(sub_mod(slot_pick<RPL>(b, ns), vnext, F.p), prod_mod<SMALLP>(ux, x, F, F32),
-                    F.p),
-            dinv[nc], F, F32);
-#pragma unroll
-        for (int t = 0; t < RPL; ++t) {
-            const int c = lane + 32 * t;
-            if (c > nc && c < r) acc[t].add(Us[l * ld + c], x);
+    for (int i = warp; i < r; i += NWARP)
+        for (int c = i + lane; c < r; c += 32) cp_async4(&Us[i * WR + c], &U[(int64_t)i * ldu + c]);
+    for (int q = warp; q < NRHS; q += NWARP) {
+        const int64_t m = m0 + q;
+        for (int c = lane; c < r; c += 32) {
+            if (IDENT) Xs[q * WR + c] = m == c ? 1u : 0u;
+            else if (m < M) cp_async4(&Xs[q * WR + c], &B[m * ldb + c]);
+            else Xs[q * WR + c] = 0u;
         }
-        x = __shfl_sync(0xFFFFFFFFu, xn, nl);
-        if (lane == 0) xs[nc] = x;
-        vnext = slot_pick<RPL>(acc, (l + 2) >> 5).value(F, w16);
     }
-    __syncwarp();
+    cp_async_wait_all();
+    __syncthreads();
+    for (int t = threadIdx.x; t < r; t += TT) dinv[t] = pow_mod(Us[t * WR + t], F.p - 2, F);
+    __syncthreads();
+
+    // inverse of diagonal block `warp`: lane c computes its column c,
+    // x_c = 1 / U_cc, x_i = -(sum_{i < l <= c} U_il x_l) / U_ii (i < c), zero below
+    const int nblk = (r + BS - 1) / BS;
+    if (warp < nblk) {
+        const int b0 = warp * BS;
+        uint32_t x[BS];
 #pragma unroll
-    for (int t = 0; t < RPL; ++t) {
-        const int c = lane + 32 * t;
-        if (c < r) B[i * ldb + c] = xs[c];
+        for (int i = BS - 1; i >= 0; --i) {
+            Dot<SMALLP> acc;
+#pragma unroll
+            for (int l = i + 1; l < BS; ++l) acc.add(Us[(b0 + i) * WR + b0 + l], x[l]);
+            const uint32_t d = b0 + i < r ? dinv[b0 + i] : 0u;
+            const uint32_t v = mul_mod(sub_mod(0u, acc.value(F, w16), F.p), d, F);
+            x[i] = (i > lane || b0 + i >= r) ? 0u : (i == lane ? d : v);
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i) Ui[(b0 + i) * BS + lane] = x[i];
+    }
+    __syncthreads();
+
+    for (int k = 0; k < nblk; ++k) {
+        const int b0 = k * BS;
+        // Y = B_k - X_{<k} U_{<k,k}: right-hand sides warp + NWARP q, column b0 + lane
+        Dot<SMALLP> acc[RPW];
+        for (int l = 0; l < b0; ++l) {
+            const uint32_t uv = Us[l * WR + b0 + lane];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) acc[q].add(Xs[(warp + NWARP * q) * WR + l], uv);
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int m = warp + NWARP * q;
+            Ys[m * BS + lane] = sub_mod(Xs[m * WR + b0 + lane], acc[q].value(F, w16), F.p);
+        }
+        __syncthreads();
+        // X_k = Y U_kk^{-1} (the inverse is zero below its diagonal and in the
+        // rows and columns past r)
+        Dot<SMALLP> acc2[RPW];
+#pragma unroll 8
+        for (int l = 0; l < BS; ++l) {
+            const uint32_t uv = Ui[(b0 + l) * BS + lane];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) acc2[q].add(Ys[(warp + NWARP * q) * BS + l], uv);
+        }
+        if (b0 + lane < r) {
+#pragma unroll
+            for (int q = 0; q < RPW; ++q)
+                Xs[(warp + NWARP * q) * WR + b0 + lane] = acc2[q].value(F, w16);
+        }
+        __syncthreads();
+    }
+    for (int q = warp; q < NRHS; q += NWARP) {
+        const int64_t m = m0 + q;
+        if (m < M)
+            for (int c = lane; c < r; c += 32) B[m * ldb + c] = Xs[q * WR + c];
     }
 }
 
 // left: B (r x other) <- T^{-1} B; otherwise B (other x r) <- B T^{-1}.  With
 // `blocks` > 0 the diagonal blocks of size min(WR, .) of T are inverted into B
 // instead (other is ignored).
-template <bool SMALLP, int RPL>
-pluq_status launch_trsm_warp(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_t other,
-                             int r, Field F, int64_t blocks, cudaStream_t st)
+template <bool SMALLP>
+pluq_status launch_trsm_blocked(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_t other,
+                                int r, Field F, int64_t blocks, cudaStream_t st)
 {
     const int rr = blocks > 0 ? (r < WR ? r : WR) : r;
     const int64_t rhs = blocks > 0 ? rr : other;
     const int64_t nb = blocks > 0 ? blocks : 1;
-    const int wpb = WPB;
-    const size_t smem = ((size_t)rr * tri_ld(rr) + (left ? 0 : WR) + (size_t)wpb * WR) * sizeof(uint32_t);
-    const dim3 grid((unsigned)ceil_div(rhs, wpb), (unsigned)nb);
-    const int nt = 32 * wpb;
-    const int full = (WR * tri_ld(WR) + WPB * WR) * 4, fullr = (WR * tri_ld(WR) + WR + WPB * WR) * 4;
+    const dim3 grid((unsigned)ceil_div(rhs, NRHS), (unsigned)nb);
 #define PLUQ_TRSM_ATTR(K, BYTES)                                                                   \
     {                                                                                             \
         static const bool attr =                                                                  \
-            cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES) ==        \
+            cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BYTES)) == \
             cudaSuccess;                                                                          \
         if (!attr) return PLUQ_ECUDA;                                                             \
     }
     if (left && blocks > 0) {
-        PLUQ_TRSM_ATTR((trsm_left_warp<SMALLP, RPL, true>), full)
-        trsm_left_warp<SMALLP, RPL, true><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, r, 0, F, WR);
+        PLUQ_TRSM_ATTR((trsm_left_blocked<SMALLP, true>), SM_LEFT)
+        trsm_left_blocked<SMALLP, true><<<grid, TT, SM_LEFT, st>>>(T, ldt, B.ptr, B.ld, r, 0, F, WR);
     } else if (left) {
-        PLUQ_TRSM_ATTR((trsm_left_warp<SMALLP, RPL, false>), full)
-        trsm_left_warp<SMALLP, RPL, false><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, r, other, F, 0);
+        PLUQ_TRSM_ATTR((trsm_left_blocked<SMALLP, false>), SM_LEFT)
+        trsm_left_blocked<SMALLP, false><<<grid, TT, SM_LEFT, st>>>(T, ldt, B.ptr, B.ld, r, other, F, 0);
     } else if (blocks > 0) {
-        PLUQ_TRSM_ATTR((trsm_right_warp<SMALLP, RPL, true>), fullr)
-        trsm_right_warp<SMALLP, RPL, true><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, 0, r, F, WR);
+        PLUQ_TRSM_ATTR((trsm_right_blocked<SMALLP, true>), SM_RIGHT)
+        trsm_right_blocked<SMALLP, true><<<grid, TT, SM_RIGHT, st>>>(T, ldt, B.ptr, B.ld, 0, r, F, WR);
     } else {
-        PLUQ_TRSM_ATTR((trsm_right_warp<SMALLP, RPL, false>), fullr)
-        trsm_right_warp<SMALLP, RPL, false><<<grid, nt, smem, st>>>(T, ldt, B.ptr, B.ld, other, r, F, 0);
+        PLUQ_TRSM_ATTR((trsm_right_blocked<SMALLP, false>), SM_RIGHT)
+        trsm_right_blocked<SMALLP, false><<<grid, TT, SM_RIGHT, st>>>(T, ldt, B.ptr, B.ld, other, r, F, 0);
     }
 #undef PLUQ_TRSM_ATTR
     return last_launch();
@@ -245,17 +312,8 @@ pluq_status launch_trsm_warp(bool left, const uint32_t *T, int64_t ldt, Blk B, i
 pluq_status trsm_direct(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_t other, int r,
                         Field F, int64_t blocks, cudaStream_t st)
 {
-    const bool sp = F.p <= 65536u;
-    const int rb = blocks > 0 ? (r < WR ? r : WR) : r;
-    const int rpl = rb <= 32 ? 1 : rb <= 64 ? 2 : 4;
-    if (sp) {
-        if (rpl == 1) return launch_trsm_warp<true, 1>(left, T, ldt, B, other, r, F, blocks, st);
-        if (rpl == 2) return launch_trsm_warp<true, 2>(left, T, ldt, B, other, r, F, blocks, st);
-        return launch_trsm_warp<true, 4>(left, T, ldt, B, other, r, F, blocks, st);
-    }
-    if (rpl == 1) return launch_trsm_warp<false, 1>(left, T, ldt, B, other, r, F, blocks, st);
-    if (rpl == 2) return launch_trsm_warp<false, 2>(left, T, ldt, B, other, r, F, blocks, st);
-    return launch_trsm_warp<false, 4>(left, T, ldt, B, other, r, F, blocks, st);
+    if (F.p <= 65536u) return launch_trsm_blocked<true>(left, T, ldt, B, other, r, F, blocks, st);
+    return launch_trsm_blocked<false>(left, T, ldt, B, other, r, F, blocks, st);
 }
 
 }  // namespace
