@@ -247,6 +247,9 @@ struct LeafShared {
     int gfail;
 };
 
+static_assert(offsetof(LeafShared, pbuf) % 16 == 0 && (LM * 4) % 16 == 0,
+              "pivot-row buffer rows must be 16-byte aligned");
+
 constexpr int NOKEY = 0x7FFFFFFF;
 constexpr uint32_t STEP_WAIT_LIMIT = 1u << 22;
 
@@ -280,7 +283,13 @@ template <bool SMALLP>
 __device__ __forceinline__ uint32_t ff_update(uint32_t d, uint32_t w, uint32_t f, uint32_t q,
                                               const Field &F, const Field32 &F32)
 {
-    if (SMALLP) return sub_mod(reduce32(d * w, F32), reduce32(f * q, F32), F32.p);
+    if (SMALLP) {
+        // p < 2^16: t = d w reduced only to [0, 2p), then t + f (p - q)
+        // <= 2p - 1 + (p - 1) p < 2^32 takes a single full reduction
+        const uint32_t dw = d * w;
+        const uint32_t t = dw - __umulhi(dw, F32.mu) * F32.p;
+        return reduce32(t + f * (F32.p - q), F32);
+    }
     return mul_sub_mul_mod(d, w, f, q, F);
 }
 
@@ -346,7 +355,7 @@ struct LAcc {
     __device__ __forceinline__ void add(uint32_t a, uint32_t b)
     {
         if (SMALLP) {
-            lo += (uint64_t)(a * b);
+            lo += (uint64_t)a * b;          // one widening multiply-add
         } else {
             lo += (uint64_t)(a & 0xFFFFu) * b;
             hi += (uint64_t)(a >> 16) * b;
@@ -423,15 +432,14 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
             bool fail = false;
 #pragma unroll 1
             for (int k = 0; k < b && !fail; ++k) {
-                if (rel == k) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) S.pbuf[k & 1][4 * sub + u] = w[u];
-                }
+                // the pivot row's four columns of this lane move as one 16-byte word
+                if (rel == k)
+                    *reinterpret_cast<uint4 *>(&S.pbuf[k & 1][4 * sub]) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
                 if (pw > 1) asm volatile("bar.sync 1, %0;" ::"r"(pw * 32) : "memory");
                 else __syncwarp();
-                uint32_t q[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) q[u] = S.pbuf[k & 1][4 * sub + u];
+                const uint4 qv = *reinterpret_cast<const uint4 *>(&S.pbuf[k & 1][4 * sub]);
+                const uint32_t q[4] = {qv.x, qv.y, qv.z, qv.w};
                 const uint32_t d = S.pbuf[k & 1][k];
                 fail = d == 0;
                 if (tid == 0) S.dval[k] = d;
