@@ -29,7 +29,7 @@ constexpr int WR = 128;            // largest triangle solved directly
 constexpr int BS = 32;             // diagonal block of the direct solver
 constexpr int NBLK = WR / BS;      // diagonal blocks of the largest triangle
 constexpr int NRHS = 32;           // right-hand sides per thread block
-constexpr int TT = 256;            // threads per block
+constexpr int TT = 512;            // threads per block
 constexpr int NWARP = TT / 32;     // warps per block
 constexpr int RPW = BS / NWARP;    // rows (left) or right-hand sides (right) per warp
 constexpr int TB = WR;             // diagonal blocks the inverses start from
