@@ -566,3 +566,40 @@ def test_nullspace_and_solve_medium():
     B2 = g.integers(0, p, (60, 2)).astype(np.uint32)
     _, ok2 = oracle.solve(A, B2, p)
     assert not ok2.any()                 # random right-hand sides miss a rank-37 image
+
+
+def test_use_pins_reject_plausible_mistakes():
+    """The checks above would catch the usual slips: a determinant without the
+    permutation signs, a kernel basis without the minus sign, a particular
+    solution with nonzero free coordinates."""
+    p = 5
+    g = np.random.Generator(np.random.PCG64(77))
+    # determinant: product of U's diagonal without sgn(P) sgn(Q)
+    caught = False
+    for _ in range(40):
+        A = g.integers(0, p, (4, 4)).astype(np.uint32)
+        LU, pp, pq, r = oracle.pluq(A, p)
+        if r < 4:
+            continue
+        unsigned = int(np.prod([int(LU[i, i]) for i in range(4)], dtype=object) % p)
+        assert oracle.determinant(A, p) == brute.leibniz_det(A, p)
+        if unsigned != brute.leibniz_det(A, p):
+            caught = True
+    assert caught
+    # nullspace: the pivot coordinates without the minus sign
+    A = np.array([[1, 2, 3, 1], [0, 1, 4, 2]], dtype=np.uint32)
+    N = oracle.right_nullspace(A, p).astype(np.int64)
+    assert not np.any(brute.matmul_mod(A, N, p))
+    _, pc = oracle.rref(A, p)
+    wrong = N.copy()
+    wrong[pc, :] = (p - wrong[pc, :]) % p
+    assert np.any(brute.matmul_mod(A, wrong, p))
+    # solve: a solution with a nonzero free coordinate is valid but not the one
+    # the definition picks
+    b = brute.matmul_mod(A, np.array([[1], [1], [1], [1]]), p).astype(np.uint32)
+    X, ok = oracle.solve(A, b, p)
+    free = np.setdiff1d(np.arange(4), pc)
+    assert ok.all() and not np.any(X[free, 0])
+    other = (X[:, 0].astype(np.int64) + N[:, 0]) % p
+    assert not np.any(brute.matmul_mod(A, other[:, None], p) - b.astype(np.int64))
+    assert np.any(other[free])
