@@ -47,14 +47,15 @@ def parse():
     ap.add_argument("--workload", default="dense_4096")
     ap.add_argument("--mm", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["pluq", "gemm", "leaf", "trsm"], default=None,
+    ap.add_argument("--profile", choices=["pluq", "gemm", "leaf", "trsm", "perm"], default=None,
                     help="untimed: one warm-up and one decomposition of the workload (pluq), one "
                          "modular product of --shape M,N,K (gemm), one base-case call on a "
-                         "uniform --shape M,N block (leaf), or the left and right triangular "
+                         "uniform --shape M,N block (leaf), the left and right triangular "
                          "solves with an r x r triangle and N right-hand sides, --shape r,N "
-                         "(trsm), each twice, for external profilers")
+                         "(trsm), or PermR and PermC of an --shape M,N matrix by random "
+                         "permutations (perm), each twice, for external profilers")
     ap.add_argument("--shape", default="8192,8192,2048",
-                    help="sizes for --profile gemm / leaf / trsm")
+                    help="sizes for --profile gemm / leaf / trsm / perm")
     ap.add_argument("--p", type=int, default=65521, help="modulus for --profile gemm")
     return ap.parse_args()
 
@@ -76,6 +77,18 @@ def run_profile_target(args):
         for _ in range(2):
             pluq.pluq_trsm_left_lower_unit(T, B.clone(), args.p, mm=args.mm)
             pluq.pluq_trsm_right_upper(T, Bt.clone(), args.p, mm=args.mm)
+    elif args.profile == "perm":
+        M, N = (int(x) for x in args.shape.split(",")[:2])
+        g = torch.Generator(device="cuda")
+        g.manual_seed(3)
+        X = torch.randint(0, args.p, (M, N), generator=g, device="cuda",
+                          dtype=torch.int64).to(torch.int32)
+        pr = torch.randperm(M, generator=g, device="cuda").to(torch.int32)
+        pc = torch.randperm(N, generator=g, device="cuda").to(torch.int32)
+        ws = torch.empty(M * N * 4, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            pluq.pluq_perm_rows(X, pr, workspace=ws)
+            pluq.pluq_perm_cols(X, pc, workspace=ws)
     elif args.profile == "gemm":
         M, N, K = (int(x) for x in args.shape.split(","))
         p = args.p
