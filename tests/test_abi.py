@@ -80,3 +80,35 @@ def test_modulus_validation_matches_trial_division():
         else:
             with pytest.raises(pluq.PluqError):
                 pluq.pluq_workspace_size(4, 4, n)
+
+
+def test_uses_reject_bad_arguments_on_the_host():
+    """The determinant / nullspace / solve entry points and their workspace
+    query validate sizes, pointers and the modulus before any device work, so
+    these calls need no GPU (the matrix pointer is never dereferenced)."""
+    import ctypes
+    lib = pluq.load()
+    out = ctypes.c_size_t(0)
+    ok, einval, enotprime = 0, -1, -2
+    assert lib.pluq_uses_workspace_size(10, 8, 9, 0, 65521, 0, ctypes.byref(out)) == einval  # r > n
+    assert lib.pluq_uses_workspace_size(10, 8, 4, -1, 65521, 0, ctypes.byref(out)) == einval  # k < 0
+    assert lib.pluq_uses_workspace_size(10, 8, 4, 0, 65521, 7, ctypes.byref(out)) == einval   # kind
+    assert lib.pluq_uses_workspace_size(10, 8, 4, 0, 65535, 0, ctypes.byref(out)) == enotprime
+    assert lib.pluq_uses_workspace_size(10, 8, 4, 3, 65521, 0, ctypes.byref(out)) == ok
+    small = out.value
+    assert lib.pluq_uses_workspace_size(10, 8, 4, 300, 65521, 0, ctypes.byref(out)) == ok
+    assert out.value >= small > 0
+    fake = 4096                                   # never dereferenced: the calls stop first
+    assert lib.pluq_determinant(fake, 4, 3, 4, fake, fake, 65521, fake, None, 0, None) == einval
+    assert lib.pluq_determinant(fake, 4, 4, 4, fake, fake, 65521, None, None, 0, None) == einval
+    assert lib.pluq_determinant(fake, 4, 4, 4, fake, fake, 65535, fake, None, 0, None) == enotprime
+    assert lib.pluq_right_nullspace(fake, 4, 4, 4, 5, fake, 65521, fake, 1, 0, None, 0,
+                                    None) == einval                                       # r > n
+    assert lib.pluq_left_nullspace(fake, 4, 4, 4, 1, fake, 65535, fake, 4, 0, None, 0,
+                                   None) == enotprime
+    assert lib.pluq_left_nullspace(fake, 4, 4, 4, 1, fake, 65521, fake, 3, 0, None, 0,
+                                   None) == einval                                        # ldk < m
+    assert lib.pluq_solve(fake, 4, 4, 4, 2, fake, fake, 65521, fake, 4, -1, fake, 4, fake, 0,
+                          None, 0, None) == einval                                        # k < 0
+    assert lib.pluq_solve(fake, 4, 4, 4, 2, fake, fake, 65521, fake, 4, 2, fake, 4, None, 0,
+                          None, 0, None) == einval                                        # no flag
