@@ -112,3 +112,25 @@ def test_uses_reject_bad_arguments_on_the_host():
                           None, 0, None) == einval                                        # k < 0
     assert lib.pluq_solve(fake, 4, 4, 4, 2, fake, fake, 65521, fake, 4, 2, fake, 4, None, 0,
                           None, 0, None) == einval                                        # no flag
+
+
+def test_autotune_cache_lookup_on_the_host(tmp_path):
+    """Workload classes round sizes up to powers of two and separate limb
+    counts and dense / deficient inputs; apply() sets the library's knobs
+    from the cache and leaves them alone for an unknown class."""
+    import json
+    from paper_1301_4438_gb300 import autotune
+    assert autotune._class_key(4096, 4096, 65521, False) == "4096x4096:L2:full"
+    assert autotune._class_key(3000, 5000, 2147483647, True) == "4096x8192:L4:def"
+    assert autotune._class_key(1, 1, 251, False) == "1x1:L1:full"
+    cache = tmp_path / "tuning.json"
+    cache.write_text(json.dumps({"256x256:L2:def": {"leaf": 64, "small_mm_macs": 1 << 25,
+                                                    "ms": 1.0}}))
+    old = pluq.pluq_get_tuning()
+    try:
+        assert autotune.apply(200, 256, 65521, deficient=True, cache=str(cache))
+        assert pluq.pluq_get_tuning() == (64, 1 << 25)
+        assert not autotune.apply(200, 256, 65521, deficient=False, cache=str(cache))
+        assert pluq.pluq_get_tuning() == (64, 1 << 25)
+    finally:
+        pluq.pluq_set_tuning(*old)
