@@ -2,9 +2,13 @@
 """Benchmark: rank-profile-revealing PLUQ mod p on one GB300 (or N replicas).
 
 One step = one PLUQ decomposition (Algorithm 1, every kernel of the hot path)
-of the workload matrix.  Default workload: 4096 x 4096 uniform mod 65521
-(dense_4096).  Metric: Gfops/s normalised by the classical elimination count
-fops(m, n, r) = 2mnr - (m + n) r^2 + (2/3) r^3.
+of the workload matrix.  Default workload: the largest single-matrix one,
+16384 x 16384 of planted rank 8192 mod 8388593 (planted_16384, three 8-bit
+limbs on the tensor cores).  Metric: Gfops/s normalised by the classical
+elimination count fops(m, n, r) = 2mnr - (m + n) r^2 + (2/3) r^3.  The same
+line carries the other workloads (256^2 planted, 4096^2 dense with both
+product forms, 8192 x 32768 planted mod 2^31 - 1, and the 2000-matrix uneven
+batch), each timed with CUDA events after its own warm-up.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,7 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dense_4096")
+    ap.add_argument("--workload", default="planted_16384")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (256^2, 4096^2, 8192x32768, batch)")
     ap.add_argument("--mm", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["pluq", "gemm", "leaf", "trsm", "perm"], default=None,
@@ -261,6 +267,128 @@ def whole_job_rate(world: int, steps: int, work_per_step: float, total_ms: float
     return world * steps * work_per_step / (total_ms / 1e3) / 1e9
 
 
+def load_workload(cfg, dev):
+    """(device int32 copy of the workload matrix, host numpy copy)."""
+    import torch
+    from paper_1301_4438_gb300 import workloads as W
+    if cfg.kind == "uniform":
+        A_host_np, _ = W.make(cfg)
+        A0 = torch.from_numpy(A_host_np.astype(np.int32)).to(dev)
+    else:
+        At, _ = W.make(cfg, device=str(dev))
+        A0 = At.to(torch.int32)
+        del At
+        A_host_np = A0.cpu().numpy()
+    return A0, A_host_np
+
+
+def tune_for(cfg, m, n, p):
+    """Recursion cutoff, product threshold and branch threshold for this
+    workload class (cached per class)."""
+    from paper_1301_4438_gb300 import autotune, pluq
+    tuned = autotune.tune(m, n, p, deficient=cfg.kind == "planted",
+                          cache=os.path.join(ROOT, "_build_tuning.json"), budget_s=60.0)
+    pluq.pluq_set_tuning(tuned[0], tuned[1])
+    pluq.pluq_set_branch_min(tuned[2])
+    return tuned
+
+
+def time_single(cfg, mm, steps, warmup, dev, flush):
+    """CUDA-event time of `steps` decompositions of one workload after `warmup`
+    untimed ones (input restored and L2 flushed between steps, outside the
+    events)."""
+    import torch
+    from paper_1301_4438_gb300 import pluq
+    A0, _ = load_workload(cfg, dev)
+    m, n, p = cfg.m, cfg.n, cfg.p
+    tuned = tune_for(cfg, m, n, p)
+    A = torch.empty_like(A0)
+    ws = torch.empty(pluq.pluq_workspace_size(m, n, p), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    times, r = [], 0
+    for it in range(warmup + steps):
+        A.copy_(A0)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, r = pluq.pluq_mod_p(A, p, mm=mm, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    out = {"m": m, "n": n, "p": p, "rank": r, "mm": mm, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms, "value": fops(m, n, r) / (ms / 1e3) / 1e9, "unit": UNIT,
+           "recipe": cfg.note,
+           "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1], "branch_min": tuned[2]}}
+    if cfg.r is not None:
+        out["rank_equals_planted"] = r == cfg.r
+    del A, A0, ws
+    return out
+
+
+def time_batch(dev, workers=16):
+    """The 2000-matrix uneven batch (m, n uniform in [64, 2048], planted rank
+    floor(min(m, n) / 2), p = 65521): the worker-pool entry point against one
+    decomposition at a time, each over the whole batch after one warm-up pass
+    on a copy."""
+    import torch
+    from paper_1301_4438_gb300 import pluq, workloads as W
+    bt = W.batch_2000()
+    originals = [W.planted_device(m, n, r, bt.p, sd, str(dev))[0]
+                 for m, n, r, sd in zip(bt.ms, bt.ns, bt.rs, bt.seeds)]
+    work = sum(fops(m, n, r) for m, n, r in zip(bt.ms, bt.ns, bt.rs))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        mats = [a.clone() for a in originals]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ranks = fn(mats)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        del mats
+        return e0.elapsed_time(e1), ranks
+
+    def pool(mats):
+        return pluq.pluq_mod_p_batched(mats, bt.p, workers=workers)[2]
+
+    ws = torch.empty(max(pluq.pluq_workspace_size(m, n, bt.p) for m, n in zip(bt.ms, bt.ns)),
+                     dtype=torch.uint8, device=dev)
+
+    def one_by_one(mats):
+        return [pluq.pluq_mod_p(a, bt.p, workspace=ws)[2] for a in mats]
+
+    timed(pool)                               # warm-up (kernels, host pools)
+    ms_pool, ranks_pool = timed(pool)
+    ms_one, ranks_one = timed(one_by_one)
+    del originals, ws
+    return {"count": len(bt.ms), "p": bt.p, "sizes": "m, n uniform in [64, 2048]",
+            "rank": "floor(min(m, n) / 2), planted", "fops_total": work,
+            "worker_pool": {"workers": workers, "ms": ms_pool,
+                            "value": work / (ms_pool / 1e3) / 1e9, "unit": UNIT},
+            "one_at_a_time": {"ms": ms_one, "value": work / (ms_one / 1e3) / 1e9, "unit": UNIT},
+            "ranks_equal_planted": ranks_pool == bt.rs and ranks_one == bt.rs}
+
+
+def other_workloads(args, dev, flush):
+    """Every other workload of the task, timed the same way as the headline."""
+    from paper_1301_4438_gb300 import workloads as W
+    out = {}
+    for name, mms, steps in (("planted_256", ("tensor",), 20),
+                             ("dense_4096", ("tensor", "simt"), 10),
+                             ("rect_8192x32768", ("tensor",), 5)):
+        if name == args.workload:
+            continue
+        for mm in mms:
+            out[f"{name}:{mm}"] = time_single(W.CONFIGS[name], mm, steps, 3, dev, flush)
+    out["batch_2000"] = time_batch(dev)
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -275,14 +403,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     cfg = W.CONFIGS[args.workload]
-    if cfg.kind == "uniform":
-        A_host_np, _ = W.make(cfg)
-        A0 = torch.from_numpy(A_host_np.astype(np.int32)).to(dev)
-    else:
-        At, _ = W.make(cfg, device=str(dev))
-        A0 = At.to(torch.int32)
-        del At
-        A_host_np = A0.cpu().numpy()
+    A0, A_host_np = load_workload(cfg, dev)
     m, n, p = cfg.m, cfg.n, cfg.p
     A = torch.empty_like(A0)
     ws = torch.empty(pluq.pluq_workspace_size(m, n, p), dtype=torch.uint8, device=dev)
@@ -303,11 +424,8 @@ def run_ours(args):
         e1.record(stream)
         return e0, e1, r
 
-    # recursion cutoff and product threshold for this workload class
-    from paper_1301_4438_gb300 import autotune
-    tuned = autotune.tune(m, n, p, deficient=cfg.kind == "planted",
-                          cache=os.path.join(ROOT, "_build_tuning.json"), budget_s=60.0)
-    pluq.pluq_set_tuning(tuned[0], tuned[1])
+    # recursion cutoff, product threshold and branch threshold for this class
+    tuned = tune_for(cfg, m, n, p)
 
     for _ in range(args.warmup):
         step(args.mm)
@@ -404,6 +522,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         st = [a.elapsed_time(b) for a, b, _ in sv]
         simt_value = work / (statistics.mean(st) / 1e3) / 1e9
+    rank_ok = (r == cfg.r) if cfg.r is not None else None
 
     # ---------------- end to end through the public API with host buffers
     A_pinned = torch.from_numpy(A_host_np.astype(np.int32)).pin_memory()
@@ -460,6 +579,10 @@ def run_ours(args):
 
     gemm_big = [gemm_rate(8192, 8192, 8192, "tensor"), gemm_rate(8192, 8192, 2048, "tensor"),
                 gemm_rate(8192, 8192, 2048, "simt")]
+    del A, A0, ws, A_pinned, out_pinned
+    extras = None
+    if not args.no_extras:
+        extras = other_workloads(args, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -481,14 +604,18 @@ def run_ours(args):
                        "l2": "flushed (256 MiB write) and input restored from a device copy "
                              "between steps, outside the timed events",
                        "parallelism": f"replicas x{world}",
+                       "rank_equals_planted": rank_ok,
                        "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1],
-                                  "source": "autotune over leaf {32,64,128} x small-product "
-                                            "threshold {2^24,2^25,2^27}"}},
+                                  "branch_min": tuned[2],
+                                  "source": "autotune, one knob at a time: leaf {32,64,128}, "
+                                            "small-product threshold {2^24,2^25,2^27}, "
+                                            "branch threshold {32,64,128,off}"}},
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,
             "kernel_classes": classes,
             "plain_cuda_core_value": simt_value,
+            "other_workloads": extras,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": launches,

@@ -316,21 +316,23 @@ pluq_status pluq_profile_read(int kernel_class, long long *h_launches, double *h
 /*
  * Allocation-free variant of the tensor-core pluq_modmm (the paper has no
  * counterpart: this exists for callers that cannot allocate device memory).
- * Some callers cannot hand the library a workspace: code running inside a
- * CUDA graph capture, where cudaMalloc is not allowed; plug-ins living in a
+ * Some callers cannot hand the library a workspace: plug-ins living in a
  * process whose device memory is owned by another allocator (a framework's
- * caching allocator that has reserved the card); latency-critical loops that
- * cannot risk an allocation failing.  This entry point computes the same
- * C <- C - A B (assign = 0) or C <- A B (assign != 0) mod p as
- * pluq_modmm(..., PLUQ_MM_TENSOR, ...) but keeps its limb planes in a fixed
+ * caching allocator that has reserved the card), or latency-critical loops
+ * that cannot risk an allocation failing part way.  This entry point
+ * computes the same C <- C - A B (assign = 0) or C <- A B (assign != 0) mod p
+ * as pluq_modmm(..., PLUQ_MM_TENSOR, ...) but keeps its limb planes in a fixed
  * device array of PLUQ_NOALLOC_SCRATCH_BYTES that the library declares
  * statically; it calls no cudaMalloc / cudaFree and no allocating routine.
  *  - Limit: the product must satisfy pluq_modmm_workspace_size(M, N, K, p,
- *    PLUQ_MM_TENSOR) <= PLUQ_NOALLOC_SCRATCH_BYTES (e.g. M = N = K = 2048 for
- *    p < 2^16); larger products return PLUQ_ENOMEM and touch nothing.
+ *    PLUQ_MM_TENSOR) <= PLUQ_NOALLOC_SCRATCH_BYTES.  For p < 2^16 (two limbs)
+ *    the largest square product is M = N = K = 2000; larger products return
+ *    PLUQ_ENOMEM and touch nothing.
  *  - The first call on each device looks up the array's device address with
- *    that device current (cudaGetSymbolAddress) and caches it; make that first
- *    call before any stream capture.
+ *    that device current (cudaGetSymbolAddress) and caches it for the life of
+ *    the process; make that first call before any stream capture.  The cached
+ *    address is not refreshed after cudaDeviceReset: do not call this entry
+ *    point on a device after resetting it.
  *  - Every call on a device shares the one array and leaves its contents
  *    behind (every byte a call reads is written by that call first).  Calls
  *    whose kernels overlap on the GPU (different streams, or several host
@@ -353,6 +355,16 @@ pluq_status pluq_modmm_tensor_noalloc(uint32_t *d_C, int64_t ldc, const uint32_t
  */
 pluq_status pluq_set_tuning(int64_t leaf, int64_t small_mm_macs);
 pluq_status pluq_get_tuning(int64_t *h_leaf, int64_t *h_small_mm_macs);
+
+/*
+ * PLUQ(F) and PLUQ(G) of a recursion node are independent (the parallelism
+ * Sec. 9 points out).  When both blocks have at least branch_min rows and
+ * columns, G runs on another host thread with its own streams and a slice of
+ * the workspace while the calling thread runs F.  Speed only, never results.
+ * Default 64; EINVAL for branch_min < 1.
+ */
+pluq_status pluq_set_branch_min(int64_t branch_min);
+int64_t pluq_get_branch_min(void);
 
 /* Number of 8-bit limbs the tensor form splits residues mod p into (1 to 4). */
 int pluq_tensor_limbs(uint32_t p);

@@ -1,12 +1,15 @@
-"""Autotuner for the recursion cutoff and the product-kernel threshold.
+"""Autotuner for the recursion cutoff, the product-kernel threshold and the
+branch threshold.
 
 The decomposition's result never depends on these knobs (the split points of
 the recursion are fixed at floor(m/2), floor(n/2); the leaf and the products
-are exact), only its speed does.  For a workload class (size rounded to a
-power of two, number of limbs of p, dense or rank-deficient) the tuner times
-`pluq_mod_p` on a seeded synthetic matrix of that class for each candidate
-(leaf size, small-product threshold) and caches the fastest in a JSON file.
-`apply()` looks the class up and sets the library's process-wide knobs.
+are exact; PLUQ(F) and PLUQ(G) are independent), only its speed does.  For a
+workload class (size rounded to a power of two, number of limbs of p, dense
+or rank-deficient) the tuner times `pluq_mod_p` on a seeded synthetic matrix
+of that class, one knob at a time from the defaults (leaf size, then
+small-product threshold, then the size above which PLUQ(G) runs on another
+host thread), and caches the fastest setting in a JSON file.  `apply()` looks
+the class up and sets the library's process-wide knobs.
 """
 from __future__ import annotations
 
@@ -21,6 +24,8 @@ from . import pluq, workloads
 
 LEAVES = (32, 64, 128)
 SMALL_MM = (1 << 24, 1 << 25, 1 << 27)
+BRANCH = (32, 64, 128, 1 << 40)          # 2^40: never hand G to another thread
+DEFAULT = (128, 1 << 25, 64)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pluq_gb300", "tuning.json")
 
 
@@ -55,40 +60,54 @@ def _sample(m, n, p, deficient, seed=7):
 
 
 def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
-         cache: str = DEFAULT_CACHE, budget_s: float = 60.0):
-    """Time every candidate on one sample of the class and cache the best.
-    Returns (leaf, small_mm_macs, ms)."""
+         cache: str = DEFAULT_CACHE, budget_s: float = 60.0, force: bool = False):
+    """Time the candidates on one sample of the class, one knob at a time, and
+    cache the best; a class already in the cache is returned as cached unless
+    `force`.  Returns (leaf, small_mm_macs, branch_min, ms)."""
     key = _class_key(m, n, p, deficient)
+    if not force:
+        ent = _load(cache).get(key)
+        if ent and "branch_min" in ent:
+            return int(ent["leaf"]), int(ent["small_mm_macs"]), int(ent["branch_min"]), ent["ms"]
     A0 = _sample(m, n, p, deficient)
     ws = torch.empty(pluq.pluq_workspace_size(m, n, p), dtype=torch.uint8, device="cuda")
     old = pluq.pluq_get_tuning()
-    best = None
+    old_branch = pluq.pluq_get_branch_min()
     t_start = time.perf_counter()
+
+    def run(cand):
+        pluq.pluq_set_tuning(cand[0], cand[1])
+        pluq.pluq_set_branch_min(cand[2])
+        times = []
+        for _ in range(reps + 1):
+            A = A0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pluq.pluq_mod_p(A, p, workspace=ws)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        return 1e3 * min(times[1:])
+
     try:
-        for leaf in LEAVES:
-            for small in SMALL_MM:
-                pluq.pluq_set_tuning(leaf, small)
-                times = []
-                for _ in range(reps + 1):
-                    A = A0.clone()
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    pluq.pluq_mod_p(A, p, workspace=ws)
-                    torch.cuda.synchronize()
-                    times.append(time.perf_counter() - t0)
-                ms = 1e3 * min(times[1:])
-                if best is None or ms < best[2]:
-                    best = (leaf, small, ms)
+        best = DEFAULT
+        best_ms = run(best)
+        for knob, options in enumerate((LEAVES, SMALL_MM, BRANCH)):
+            for v in options:
                 if time.perf_counter() - t_start > budget_s:
                     break
-            if time.perf_counter() - t_start > budget_s:
-                break
+                cand = tuple(v if i == knob else best[i] for i in range(3))
+                if cand == best:
+                    continue
+                ms = run(cand)
+                if ms < best_ms:
+                    best, best_ms = cand, ms
     finally:
         pluq.pluq_set_tuning(*old)
+        pluq.pluq_set_branch_min(old_branch)
     data = _load(cache)
-    data[key] = {"leaf": best[0], "small_mm_macs": best[1], "ms": best[2]}
+    data[key] = {"leaf": best[0], "small_mm_macs": best[1], "branch_min": best[2], "ms": best_ms}
     _store(cache, data)
-    return best
+    return best[0], best[1], best[2], best_ms
 
 
 def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_CACHE) -> bool:
@@ -97,4 +116,6 @@ def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_
     if not ent:
         return False
     pluq.pluq_set_tuning(int(ent["leaf"]), int(ent["small_mm_macs"]))
+    if "branch_min" in ent:
+        pluq.pluq_set_branch_min(int(ent["branch_min"]))
     return True

@@ -200,6 +200,22 @@ void start(int cls, cudaStream_t st);
 void stop(int cls, cudaStream_t st, double work);
 }  // namespace prof
 
+// Dynamic shared memory above 48 KB must be opted into per kernel with
+// cudaFuncSetAttribute, which acts on the current device only: do it once per
+// device (bit `dev` of the caller's mask; devices past 63 every time).
+inline bool smem_attr_once(const void *kernel, size_t bytes, std::atomic<uint64_t> &done)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return true;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return false;
+    if (bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return true;
+}
+
 // Every kernel launch goes through here: error check and launch count.
 inline pluq_status last_launch()
 {
@@ -230,6 +246,22 @@ pluq_status launch_mm_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *
                          int64_t batch, int64_t sA, int64_t sB, int64_t sC, Arena &ar,
                          cudaStream_t st);
 size_t mm_tc_workspace(int64_t M, int64_t N, int64_t K, uint32_t p, int64_t batch);
+
+// Independent products that share K, one split launch and one persistent
+// tensor-core launch for all of them (at most two per group).
+struct MMSpec {
+    Blk C;
+    const uint32_t *A;
+    int64_t lda;
+    const uint32_t *B;
+    int64_t ldb;
+    int64_t M, N;
+    int mode;
+    int64_t batch, sA, sB, sC;
+};
+pluq_status launch_mm_tc_group(const MMSpec *spec, int count, int64_t K, Field F, Arena &ar,
+                               cudaStream_t st);
+size_t mm_tc_group_workspace(const MMSpec *spec, int count, int64_t K, uint32_t p);
 // Nonzero if a tensor-core kernel gave up on a bounded wait since the last
 // call (reads and clears the device word).
 int tc_error_flag();
@@ -239,6 +271,23 @@ pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uin
                       int64_t ldb, int64_t M, int64_t N, int64_t K, Field F, int mode,
                       int64_t batch, int64_t sA, int64_t sB, int64_t sC, Arena &ar,
                       cudaStream_t st);
+
+// In-place PermR / PermC of Sec. 2 on a block: rows (by_rows) or columns of
+// the rows x cols block at X are replaced by rows / columns map[.] - moff of
+// it.  launch_perm_ops applies up to four such ops on disjoint blocks in one
+// launch (each element read and written once); an op whose staging does not
+// fit a thread block's shared memory goes through `scratch` instead (gather,
+// then copy back).
+struct PermOp {
+    uint32_t *X;
+    int64_t ld;
+    int64_t rows, cols;
+    const int32_t *map;
+    int32_t moff;
+    bool by_rows;
+};
+pluq_status launch_perm_ops(const PermOp *ops, int count, uint32_t *scratch, size_t scratch_elems,
+                            cudaStream_t st);
 
 // Row/column gathers: dst[i][j] = src[rmap(i)][cmap(j)], maps optional.
 pluq_status launch_gather(Blk dst, const uint32_t *src, int64_t lds, int64_t rows,

@@ -8,11 +8,16 @@
 // a block go through a scratch copy.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <functional>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
 #include <stdlib.h>
+#include <stdio.h>
 #include <string.h>
 
 #include "common.cuh"
@@ -35,6 +40,9 @@ pluq_status launch_any_nonzero(const uint32_t *A, int64_t lda, int64_t m, int64_
 
 std::atomic<int64_t> g_tune_small_mm{1ll << 25};
 std::atomic<int64_t> g_tune_leaf{128};
+// PLUQ(G) goes to another host thread when F and G both have at least this
+// many rows and columns (a free branch context permitting)
+std::atomic<int64_t> g_tune_branch{64};
 
 namespace {
 // byte ranges [lo, hi) spanned by a batch of strided blocks
@@ -66,6 +74,33 @@ pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uin
             return launch_mm_simt(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, st);
     }
     return launch_mm_tc(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, ar, st);
+}
+
+// Products that share K, each to the CUDA-core kernel when launch_mm would
+// send it there and otherwise all together in one grouped tensor-core launch.
+pluq_status launch_mm_group(int kind, const MMSpec *q, int count, int64_t K, Field F, Arena &ar,
+                            cudaStream_t st)
+{
+    MMSpec tc[2];
+    int ntc = 0;
+    for (int i = 0; i < count; ++i) {
+        const MMSpec &x = q[i];
+        if (x.M <= 0 || x.N <= 0 || x.batch <= 0) continue;
+        bool simt = kind == PLUQ_MM_SIMT;
+        if (!simt && K > 0 &&
+            (double)x.M * x.N * K * x.batch <= (double)g_tune_small_mm.load(std::memory_order_relaxed)) {
+            Span sc = span(x.C.ptr, x.C.ld, x.M, x.N, x.batch, x.sC);
+            simt = !overlap(sc, span(x.A, x.lda, x.M, K, x.batch, x.sA)) &&
+                   !overlap(sc, span(x.B, x.ldb, K, x.N, x.batch, x.sB));
+        }
+        if (simt || ntc == 2)
+            PLUQ_TRY(launch_mm(simt ? PLUQ_MM_SIMT : kind, x.C, x.A, x.lda, x.B, x.ldb, x.M, x.N, K,
+                               F, x.mode, x.batch, x.sA, x.sB, x.sC, ar, st));
+        else
+            tc[ntc++] = x;
+    }
+    if (ntc == 0) return PLUQ_OK;
+    return launch_mm_tc_group(tc, ntc, K, F, ar, st);
 }
 
 namespace {
@@ -117,8 +152,32 @@ void release_words(HostWords *w)
 
 // wait for a kernel to publish sequence number `seq` in host word `at`; the
 // stream is queried now and then so that a failed launch cannot hang the host
+// Host-side instrumentation (PLUQ_HOST_STATS=1 in the environment): after
+// each decomposition, stderr gets the wall time, the summed time host threads
+// spent waiting for leaf / zero-test results, and the number of waits.
+const bool g_host_stats = getenv("PLUQ_HOST_STATS") != nullptr;
+std::atomic<long long> g_wait_ns{0}, g_waits{0};
+
+long long now_ns()
+{
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
 pluq_status wait_words(HostWords *hw, int32_t seq, cudaStream_t st, int at = 0)
 {
+    const long long t0 = g_host_stats ? now_ns() : 0;
+    struct Acc {
+        long long t0;
+        ~Acc()
+        {
+            if (g_host_stats) {
+                g_wait_ns.fetch_add(now_ns() - t0, std::memory_order_relaxed);
+                g_waits.fetch_add(1, std::memory_order_relaxed);
+            }
+        }
+    } acc{t0};
     for (long long it = 0;; ++it) {
         if (hw->h[at] == seq) return PLUQ_OK;
         if ((it & 0xFFFF) == 0xFFFF) {
@@ -126,8 +185,160 @@ pluq_status wait_words(HostWords *hw, int32_t seq, cudaStream_t st, int at = 0)
             if (e == cudaSuccess) return hw->h[at] == seq ? PLUQ_OK : PLUQ_EINTERNAL;
             if (e != cudaErrorNotReady) return PLUQ_ECUDA;
         }
+        // several branch threads may wait at once: after a short spin, give
+        // the core to the others
+        if (it > 4096) std::this_thread::yield();
     }
 }
+
+// Streams and events of one recursion context, cached per device and reused
+// across calls: creating them costs tens of microseconds each, a fixed cost
+// that small decompositions would otherwise pay on every call.
+struct Streams {
+    int dev = -1;
+    cudaStream_t st = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
+};
+std::mutex g_streams_mu;
+std::vector<Streams *> g_streams_free;
+
+Streams *acquire_streams()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_streams_mu);
+        for (size_t i = 0; i < g_streams_free.size(); ++i)
+            if (g_streams_free[i]->dev == dev) {
+                Streams *s = g_streams_free[i];
+                g_streams_free[i] = g_streams_free.back();
+                g_streams_free.pop_back();
+                return s;
+            }
+    }
+    Streams *s = new (std::nothrow) Streams;
+    if (!s) return nullptr;
+    s->dev = dev;
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess) {
+        if (s->st) cudaStreamDestroy(s->st);
+        if (s->side) cudaStreamDestroy(s->side);
+        if (s->fork) cudaEventDestroy(s->fork);
+        if (s->join) cudaEventDestroy(s->join);
+        if (s->done) cudaEventDestroy(s->done);
+        delete s;
+        return nullptr;
+    }
+    return s;
+}
+
+void release_streams(Streams *s)
+{
+    if (!s) return;
+    std::lock_guard<std::mutex> lk(g_streams_mu);
+    g_streams_free.push_back(s);
+}
+
+// Host threads that run PLUQ(G) while the thread that reached the node runs
+// PLUQ(F).  A task is only handed to a worker that is idle at that moment;
+// when none is, the caller runs the task itself, so no task ever waits for a
+// worker (a waiting parent can never block the child it waits on).
+class Workers {
+  public:
+    static Workers &get()
+    {
+        static Workers w;
+        return w;
+    }
+    bool try_run(std::function<void()> fn)
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (auto &sl : slots_)
+            if (!sl->busy) {
+                sl->busy = true;
+                sl->fn = std::move(fn);
+                sl->cv.notify_one();
+                return true;
+            }
+        if ((int)slots_.size() >= cap_) return false;
+        std::unique_ptr<Slot> sl(new (std::nothrow) Slot);
+        if (!sl) return false;
+        sl->busy = true;
+        sl->fn = std::move(fn);
+        Slot *raw = sl.get();
+        try {
+            raw->th = std::thread([this, raw] { loop(raw); });
+        } catch (...) {
+            return false;
+        }
+        slots_.push_back(std::move(sl));
+        return true;
+    }
+    ~Workers()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            for (auto &sl : slots_) {
+                sl->stop = true;
+                sl->cv.notify_one();
+            }
+        }
+        for (auto &sl : slots_)
+            if (sl->th.joinable()) sl->th.join();
+    }
+
+  private:
+    struct Slot {
+        std::thread th;
+        std::condition_variable cv;
+        std::function<void()> fn;
+        bool busy = false, stop = false;
+    };
+    Workers()
+    {
+        const int hc = (int)std::thread::hardware_concurrency();
+        cap_ = std::max(1, std::min(30, hc - 2));
+    }
+    void loop(Slot *sl)
+    {
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            sl->cv.wait(lk, [sl] { return sl->stop || (bool)sl->fn; });
+            if (!sl->fn) return;
+            std::function<void()> fn = std::move(sl->fn);
+            sl->fn = nullptr;
+            lk.unlock();
+            fn();
+            lk.lock();
+            sl->busy = false;
+            if (sl->stop) return;
+        }
+    }
+    std::mutex mu_;
+    std::vector<std::unique_ptr<Slot>> slots_;
+    int cap_ = 1;
+};
+
+// completion flag of a task handed to a worker
+struct Join {
+    std::mutex mu;
+    std::condition_variable cv;
+    bool done = false;
+    void set()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        done = true;
+        cv.notify_all();
+    }
+    void wait()
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [this] { return done; });
+    }
+};
 
 // Host words 8 + 2d (sequence number) and 9 + 2d (flag) carry the zero test of
 // the node at recursion depth d < ZDEPTH; word 0..3 belong to the leaf.
@@ -138,7 +349,8 @@ struct Ctx {
     int kind = 0;
     cudaStream_t st = nullptr;
     Arena ar;                       // scratch for products / TRSM (stack discipline)
-    uint32_t *gather = nullptr;     // m*n scratch for permutations
+    uint32_t *gather = nullptr;     // scratch for permutations too large to stage on chip
+    size_t gather_elems = 0;
     uint32_t *icopy = nullptr;      // copy of I (r3 x r2)
     int32_t *smap = nullptr, *tmap = nullptr;   // S and T index maps of the current node
     int32_t *vstack = nullptr;      // child permutation vectors (stack discipline)
@@ -150,21 +362,37 @@ struct Ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_done = nullptr;          // end of this context's work (branch contexts)
     struct BranchPool *pool = nullptr;      // contexts free to run PLUQ(G) on another thread
+    int64_t cap_m = 0, cap_n = 0;           // largest block this context's scratch serves
+    int dev = 0;                            // device of the decomposition
     int64_t leaves = 0;
     int64_t zero_checks = 0;
 };
 
 // Contexts that can each run one recursive call on a host thread of its own,
-// with their own streams, host words and scratch (sized for a quarter of the
-// matrix: the block G of any node fits).
+// with their own streams, host words and scratch.  They come in tiers: tier t
+// serves blocks of up to ceil(m / 2^(t+1)) x ceil(n / 2^(t+1)) (the block G of a
+// node at depth t fits), so PLUQ(F) and PLUQ(G) can run side by side at every
+// level of the recursion, not only near the top.
+constexpr int NTIER = 4;
+constexpr int TIER_COUNT[NTIER] = {2, 3, 4, 6};
+constexpr int NBRANCH = 2 + 3 + 4 + 6;      // branch contexts per decomposition
+constexpr int64_t BRANCH_MATRIX_MIN = 256;  // matrices below this get no branch contexts
+
 struct BranchPool {
     std::mutex mu;
     std::vector<Ctx *> free;
-    Ctx *take()
+    // the free context with the least scratch that still holds an mb x nb block
+    Ctx *take(int64_t mb, int64_t nb)
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (free.empty()) return nullptr;
-        Ctx *c = free.back();
+        int best = -1;
+        for (int i = 0; i < (int)free.size(); ++i)
+            if (free[i]->cap_m >= mb && free[i]->cap_n >= nb &&
+                (best < 0 || free[i]->cap_m * free[i]->cap_n < free[best]->cap_m * free[best]->cap_n))
+                best = i;
+        if (best < 0) return nullptr;
+        Ctx *c = free[best];
+        free[best] = free.back();
         free.pop_back();
         return c;
     }
@@ -174,9 +402,6 @@ struct BranchPool {
         free.push_back(c);
     }
 };
-constexpr int NBRANCH = 3;            // branch contexts per decomposition
-constexpr int64_t BRANCH_MIN = 256;   // both F and G at least this large in each dimension
-constexpr int64_t BRANCH_MATRIX_MIN = 1024;   // matrices below this get no branch contexts
 
 // Leaf size of the recursion (pluq_set_tuning; PLUQ_LEAF in the environment
 // sets the initial value).  Smaller leaves mean less one-SM elimination work
@@ -211,14 +436,25 @@ int32_t *vtake(Ctx &c, int64_t len)
     return v;
 }
 
-// rows [0, rows) x cols [0, cols) of the block X <- gathered with maps (in place
-// through the scratch copy)
-pluq_status permute_block(Ctx &c, uint32_t *X, int64_t ldx, int64_t rows, int64_t cols,
-                          const int32_t *rmap, const int32_t *cmap)
+// In-place row / column permutations of disjoint blocks, issued in one launch
+// (ops with a null map are identities and dropped).
+struct PermBatch {
+    PermOp op[4];
+    int n = 0;
+    void rows(uint32_t *X, int64_t ld, int64_t nr, int64_t nc, const int32_t *map, int32_t moff = 0)
+    {
+        if (nr > 0 && nc > 0 && map) op[n++] = PermOp{X, ld, nr, nc, map, moff, true};
+    }
+    void cols(uint32_t *X, int64_t ld, int64_t nr, int64_t nc, const int32_t *map, int32_t moff = 0)
+    {
+        if (nr > 0 && nc > 0 && map) op[n++] = PermOp{X, ld, nr, nc, map, moff, false};
+    }
+};
+
+pluq_status run_perms(Ctx &c, const PermBatch &b)
 {
-    if (rows <= 0 || cols <= 0 || (!rmap && !cmap)) return PLUQ_OK;
-    PLUQ_TRY(launch_gather(Blk{c.gather, cols}, X, ldx, rows, cols, rmap, cmap, c.st));
-    return launch_copy(Blk{X, ldx}, c.gather, cols, rows, cols, c.st);
+    if (b.n == 0) return PLUQ_OK;
+    return launch_perm_ops(b.op, b.n, c.gather, c.gather_elems, c.st);
 }
 
 // True when the (start, length) segments, taken in turn, walk 0, 1, 2, ...:
@@ -297,9 +533,13 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     }
     const int64_t r1 = s1.r;
     const bool deficient = r1 < (k < h ? k : h);
-    // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
-    PLUQ_TRY(permute_block(c, at(0, h), lda, k, n - h, vec(p1, s1.pid), nullptr));
-    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, h, nullptr, vec(q1, s1.qid)));
+    // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T (disjoint blocks, one launch)
+    {
+        PermBatch pb;
+        pb.rows(at(0, h), lda, k, n - h, vec(p1, s1.pid));
+        pb.cols(at(k, 0), lda, m - k, h, vec(q1, s1.qid));
+        PLUQ_TRY(run_perms(c, pb));
+    }
     // D <- L1^{-1} B1 ; E <- C1 U1^{-1}, then [F;H] <- [B2;A4] - [M1;E] D and
     // G <- C2 - E V1: each pair is independent (disjoint outputs, shared
     // read-only operands).  The second of a pair runs on the side stream when
@@ -323,40 +563,23 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
             PLUQ_TRY(trsm_right_upper(A, lda, Blk{at(k, 0), lda}, m - k, r1, F, c.kind, c.ar, c.st));
         }
     }
-    {
-        const uint32_t p = F.p;
-        const bool tc = c.kind != PLUQ_MM_SIMT;
-        const size_t need1 = tc ? mm_tc_workspace(m - r1, n - h, r1, p, 1) : 0;
-        const size_t need2 = tc ? mm_tc_workspace(m - k, h - r1, r1, p, 1) : 0;
-        Arena a2 = c.ar;
-        a2.off = align_up(c.ar.off + need1, 1024);
-        const bool both = r1 > 0 && m - r1 > 0 && n - h > 0 && m - k > 0 && h - r1 > 0;
-        cudaStream_t s2 = c.st;
-        if (c.side && both && a2.off + need2 <= c.ar.size) {
-            PLUQ_CUDA_TRY(cudaEventRecord(c.ev_fork, c.st));
-            PLUQ_CUDA_TRY(cudaStreamWaitEvent(c.side, c.ev_fork, 0));
-            s2 = c.side;
-        } else {
-            a2 = c.ar;
-        }
-        PLUQ_TRY(launch_mm(c.kind, Blk{at(r1, h), lda}, at(r1, 0), lda, at(0, h), lda, m - r1,
-                           n - h, r1, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
-        PLUQ_TRY(launch_mm(c.kind, Blk{at(k, r1), lda}, at(k, 0), lda, at(0, r1), lda, m - k,
-                           h - r1, r1, F, MM_SUB, 1, 0, 0, 0, a2, s2));
-        if (s2 != c.st) {
-            PLUQ_CUDA_TRY(cudaEventRecord(c.ev_join, c.side));
-            PLUQ_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_join, 0));
-        }
+    // [F;H] <- [B2;A4] - [M1;E] D and G <- C2 - E V1 share K = r1: one
+    // grouped launch (disjoint outputs, read-only operands)
+    if (r1 > 0) {
+        const MMSpec q[2] = {
+            {Blk{at(r1, h), lda}, at(r1, 0), lda, at(0, h), lda, m - r1, n - h, MM_SUB, 1, 0, 0, 0},
+            {Blk{at(k, r1), lda}, at(k, 0), lda, at(0, r1), lda, m - k, h - r1, MM_SUB, 1, 0, 0, 0}};
+        PLUQ_TRY(launch_mm_group(c.kind, q, 2, r1, F, c.ar, c.st));
     }
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
     // PLUQ(F) and PLUQ(G) work on disjoint blocks with their own permutation
     // vectors: with a free branch context, G runs on another host thread and
-    // stream while this thread does F (the concurrency noted in Sec. 8)
+    // stream while this thread does F (the concurrency noted in Sec. 9)
     Res s2, s3;
     Ctx *bc = nullptr;
-    if (c.pool && k - r1 >= BRANCH_MIN && n - h >= BRANCH_MIN && m - k >= BRANCH_MIN &&
-        h - r1 >= BRANCH_MIN)
-        bc = c.pool->take();
+    const int64_t bmin = g_tune_branch.load(std::memory_order_relaxed);
+    if (c.pool && k - r1 >= bmin && n - h >= bmin && m - k >= bmin && h - r1 >= bmin)
+        bc = c.pool->take(m - k, h - r1);
     if (bc) {
         pluq_status sg = PLUQ_OK, sf = PLUQ_OK;
         if (cudaEventRecord(c.ev_fork, c.st) != cudaSuccess ||
@@ -364,17 +587,14 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
             c.pool->give(bc);
             return PLUQ_ECUDA;
         }
-        std::thread th;
-        bool spawned = true;
-        try {
-            th = std::thread([&] {
-                sg = rec(*bc, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient);
-            });
-        } catch (...) {
-            spawned = false;    // no thread to be had: G on this thread, on bc's stream
-        }
+        Join jn;
+        const bool handed = Workers::get().try_run([&] {
+            if (cudaSetDevice(bc->dev) != cudaSuccess) sg = PLUQ_ECUDA;
+            else sg = rec(*bc, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient);
+            jn.set();
+        });
         sf = rec(c, at(r1, h), k - r1, n - h, lda, p2, q2, s2, depth + 1, deficient);
-        if (spawned) th.join();
+        if (handed) jn.wait();
         else sg = rec(*bc, at(k, r1), m - k, h - r1, lda, p3, q3, s3, depth + 1, deficient);
         const bool ok = cudaEventRecord(bc->ev_done, bc->st) == cudaSuccess &&
                         cudaStreamWaitEvent(c.st, bc->ev_done, 0) == cudaSuccess;
@@ -388,12 +608,20 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     }
     const int64_t r2 = s2.r, r3 = s3.r;
     int32_t *P2 = vec(p2, s2.pid), *Q2 = vec(q2, s2.qid), *P3 = vec(p3, s3.pid), *Q3 = vec(q3, s3.qid);
-    // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
-    PLUQ_TRY(permute_block(c, at(k, h), lda, m - k, n - h, P3, Q2));
-    PLUQ_TRY(permute_block(c, at(k, 0), lda, m - k, r1, P3, nullptr));
-    PLUQ_TRY(permute_block(c, at(r1, 0), lda, k - r1, r1, P2, nullptr));
-    PLUQ_TRY(permute_block(c, at(0, h), lda, r1, n - h, nullptr, Q2));
-    PLUQ_TRY(permute_block(c, at(0, r1), lda, r1, h - r1, nullptr, Q3));
+    // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T:
+    // the row permutations in one launch, then the column permutations (H
+    // takes both; G and F, already factored, sit between the pieces and stay)
+    {
+        PermBatch pr, pc;
+        pr.rows(at(k, 0), lda, m - k, r1, P3);
+        pr.rows(at(k, h), lda, m - k, n - h, P3);
+        pr.rows(at(r1, 0), lda, k - r1, r1, P2);
+        pc.cols(at(0, h), lda, r1, n - h, Q2);
+        pc.cols(at(k, h), lda, m - k, n - h, Q2);
+        pc.cols(at(0, r1), lda, r1, h - r1, Q3);
+        PLUQ_TRY(run_perms(c, pr));
+        PLUQ_TRY(run_perms(c, pc));
+    }
     // [I;K] <- [H1;H3] U2^{-1}
     const uint32_t *U2 = at(r1, h);
     PLUQ_TRY(trsm_right_upper(U2, lda, Blk{at(k, h), lda}, m - k, r2, F, c.kind, c.ar, c.st));
@@ -401,13 +629,17 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     if (r3 > 0 && r2 > 0) PLUQ_TRY(launch_copy(Blk{c.icopy, r2}, at(k, h), lda, r3, r2, c.st));
     const uint32_t *L3 = at(k, r1);
     PLUQ_TRY(trsm_left_lower_unit(L3, lda, Blk{at(k, h), lda}, r3, n - h, F, c.kind, c.ar, c.st));
-    // O <- N - J V2
-    PLUQ_TRY(launch_mm(c.kind, Blk{at(k, h + r2), lda}, at(k, h), lda, at(r1, h + r2), lda, r3,
-                       n - h - r2, r2, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
+    // O <- N - J V2 and R <- H4 - K V2 share K = r2 (disjoint outputs): one
+    // grouped launch; then I goes back and R <- R - M3 O
+    if (r2 > 0) {
+        const MMSpec q[2] = {
+            {Blk{at(k, h + r2), lda}, at(k, h), lda, at(r1, h + r2), lda, r3, n - h - r2, MM_SUB, 1,
+             0, 0, 0},
+            {Blk{at(k + r3, h + r2), lda}, at(k + r3, h), lda, at(r1, h + r2), lda, m - k - r3,
+             n - h - r2, MM_SUB, 1, 0, 0, 0}};
+        PLUQ_TRY(launch_mm_group(c.kind, q, 2, r2, F, c.ar, c.st));
+    }
     if (r3 > 0 && r2 > 0) PLUQ_TRY(launch_copy(Blk{at(k, h), lda}, c.icopy, r2, r3, r2, c.st));
-    // R <- H4 - K V2 - M3 O
-    PLUQ_TRY(launch_mm(c.kind, Blk{at(k + r3, h + r2), lda}, at(k + r3, h), lda, at(r1, h + r2),
-                       lda, m - k - r3, n - h - r2, r2, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     PLUQ_TRY(launch_mm(c.kind, Blk{at(k + r3, h + r2), lda}, at(k + r3, r1), lda, at(k, h + r2),
                        lda, m - k - r3, n - h - r2, r3, F, MM_SUB, 1, 0, 0, 0, c.ar, c.st));
     // R = P4 [L4;M4][U4 V4] Q4
@@ -416,9 +648,13 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
                  deficient));
     const int64_t r4 = s4.r;
     int32_t *P4 = vec(p4, s4.pid), *Q4 = vec(q4, s4.qid);
-    // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T
-    PLUQ_TRY(permute_block(c, at(k + r3, 0), lda, m - k - r3, h + r2, P4, nullptr));
-    PLUQ_TRY(permute_block(c, at(0, h + r2), lda, k + r3, n - h - r2, nullptr, Q4));
+    // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T (disjoint, one launch)
+    {
+        PermBatch pb;
+        pb.rows(at(k + r3, 0), lda, m - k - r3, h + r2, P4);
+        pb.cols(at(0, h + r2), lda, k + r3, n - h - r2, Q4);
+        PLUQ_TRY(run_perms(c, pb));
+    }
     // P, Q and the block permutations S, T ; A <- S^T A T^T
     const int64_t sseg[4][2] = {{0, r1 + r2}, {k, r3 + r4}, {r1 + r2, k - r1 - r2},
                                 {k + r3 + r4, m - k - r3 - r4}};
@@ -432,9 +668,20 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
         PLUQ_TRY(launch_compose(vec(p1, s1.pid), P2, P3, P4, vec(q1, s1.qid), Q2, Q3, Q4, pp, pq,
                                 c.smap, c.tmap, m, n, k, h, r1, r2, r3, r4, c.st));
     }
-    if (!s_ident || !t_is_id)
-        PLUQ_TRY(permute_block(c, A, lda, m, n, s_ident ? nullptr : c.smap,
-                               t_is_id ? nullptr : c.tmap));
+    // S only moves rows [r1+r2, k+r3+r4) and T only columns [r1, h+r2+r4) (the
+    // segments before and after stay), so the passes cover those bands
+    if (!s_ident) {
+        PermBatch pb;
+        const int64_t b0 = r1 + r2, b1 = k + r3 + r4;
+        pb.rows(at(b0, 0), lda, b1 - b0, n, c.smap + b0, (int32_t)b0);
+        PLUQ_TRY(run_perms(c, pb));
+    }
+    if (!t_is_id) {
+        PermBatch pb;
+        const int64_t b0 = r1, b1 = h + r2 + r4;
+        pb.cols(at(0, b0), lda, m, b1 - b0, c.tmap + b0, (int32_t)b0);
+        PLUQ_TRY(run_perms(c, pb));
+    }
     c.vtop = vmark;
     return PLUQ_OK;
 }
@@ -451,7 +698,7 @@ Layout layout_core(int64_t m, int64_t n, uint32_t p, int kind)
 {
     Layout L{};
     const int64_t mn = m < n ? m : n;
-    L.gather = align_up((size_t)m * n * 4 + 256, 256);
+    L.gather = align_up((size_t)m * (n + 4) * 4 + 256, 256);
     L.icopy = align_up((size_t)((m + 1) / 2) * ((n + 1) / 2) * 4 + 256, 256);
     L.maps = align_up((size_t)(m + n + 2) * 4, 256);
     L.vstack = align_up((size_t)(8 * (m + n) + 64 * 64) * 4, 256);
@@ -465,9 +712,12 @@ Layout layout_core(int64_t m, int64_t n, uint32_t p, int kind)
 
 bool has_branches(int64_t m, int64_t n) { return m >= BRANCH_MATRIX_MIN && n >= BRANCH_MATRIX_MIN; }
 
-// the main context, then NBRANCH branch contexts for ceil(m/2) x ceil(n/2)
+// block sides tier t of the branch contexts serves: ceil(x / 2^(t+1))
+int64_t tier_dim(int64_t x, int t) { return (x + (2ll << t) - 1) >> (t + 1); }
+
+// the main context, then TIER_COUNT[t] branch contexts of each tier t
 struct Layout2 {
-    Layout main, branch;
+    Layout main, branch[NTIER];
     size_t total;
 };
 Layout2 layout(int64_t m, int64_t n, uint32_t p, int kind, bool branches = true)
@@ -476,8 +726,10 @@ Layout2 layout(int64_t m, int64_t n, uint32_t p, int kind, bool branches = true)
     L.main = layout_core(m, n, p, kind);
     L.total = L.main.total;
     if (branches && has_branches(m, n)) {
-        L.branch = layout_core((m + 1) / 2, (n + 1) / 2, p, kind);
-        L.total += NBRANCH * L.branch.total;
+        for (int t = 0; t < NTIER; ++t) {
+            L.branch[t] = layout_core(tier_dim(m, t), tier_dim(n, t), p, kind);
+            L.total += TIER_COUNT[t] * L.branch[t].total;
+        }
     }
     return L;
 }
@@ -485,7 +737,9 @@ Layout2 layout(int64_t m, int64_t n, uint32_t p, int kind, bool branches = true)
 // carve one context's scratch out of w (advancing w)
 void carve(Ctx &c, const Layout &L, int64_t m, char *&w)
 {
-    c.gather = (uint32_t *)w; w += L.gather;
+    c.gather = (uint32_t *)w;
+    c.gather_elems = L.gather / 4;
+    w += L.gather;
     c.icopy = (uint32_t *)w; w += L.icopy;
     c.smap = (int32_t *)w;
     c.tmap = c.smap + m;
@@ -547,6 +801,15 @@ pluq_status pluq_get_tuning(int64_t *h_leaf, int64_t *h_small_mm_macs)
     *h_small_mm_macs = g_tune_small_mm.load();
     return PLUQ_OK;
 }
+
+pluq_status pluq_set_branch_min(int64_t branch_min)
+{
+    if (branch_min < 1) return PLUQ_EINVAL;
+    g_tune_branch.store(branch_min);
+    return PLUQ_OK;
+}
+
+int64_t pluq_get_branch_min(void) { return g_tune_branch.load(); }
 int64_t pluq_leaf_max_rows(void) { return LEAF_MAX; }
 int64_t pluq_leaf_max_cols(void) { return LEAF_MAX; }
 
@@ -576,59 +839,64 @@ pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p
         PLUQ_TRY(launch_iota(d_perm_q, n, st));
         return PLUQ_OK;
     }
+    int dev = 0;
+    PLUQ_CUDA_TRY(cudaGetDevice(&dev));
     Ctx c;
     c.F = make_field(p);
     c.kind = kind;
     c.st = st;
+    c.dev = dev;
     carve(c, L.main, m, w);
+    c.cap_m = m;
+    c.cap_n = n;
     c.hw = hw;
     c.leaf = leaf_size();
-    // streams, events and host words of this decomposition's contexts live
-    // until it returns
+    // streams, events and host words of this decomposition's contexts are
+    // held until it returns (then handed back to the process-wide pools)
     Ctx branch[NBRANCH];
+    Streams *sbs[NBRANCH + 1] = {};
     BranchPool pool;
     struct Guard {
-        Ctx &c;
         Ctx *b;
+        Streams **sbs;
         ~Guard()
         {
-            auto drop = [](Ctx &x, bool own_stream) {
-                if (x.ev_fork) cudaEventDestroy(x.ev_fork);
-                if (x.ev_join) cudaEventDestroy(x.ev_join);
-                if (x.ev_done) cudaEventDestroy(x.ev_done);
-                if (x.side) cudaStreamDestroy(x.side);
-                if (own_stream && x.st) cudaStreamDestroy(x.st);
-            };
-            drop(c, false);
-            for (int i = 0; i < NBRANCH; ++i) {
-                drop(b[i], true);
+            for (int i = 0; i < NBRANCH; ++i)
                 if (b[i].hw) release_words(b[i].hw);
-            }
+            for (int i = 0; i <= NBRANCH; ++i) release_streams(sbs[i]);
         }
-    } guard{c, branch};
-    auto make_streams = [](Ctx &x) {
-        return cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking) == cudaSuccess &&
-               cudaEventCreateWithFlags(&x.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-               cudaEventCreateWithFlags(&x.ev_join, cudaEventDisableTiming) == cudaSuccess &&
-               cudaEventCreateWithFlags(&x.ev_done, cudaEventDisableTiming) == cudaSuccess;
+    } guard{branch, sbs};
+    auto bind = [](Ctx &x, Streams *sb, bool own_stream) {
+        x.side = sb->side;
+        x.ev_fork = sb->fork;
+        x.ev_join = sb->join;
+        x.ev_done = sb->done;
+        if (own_stream) x.st = sb->st;
     };
-    if (!make_streams(c)) return PLUQ_ECUDA;
+    sbs[NBRANCH] = acquire_streams();
+    if (!sbs[NBRANCH]) return PLUQ_ECUDA;
+    bind(c, sbs[NBRANCH], false);
     if (branches && has_branches(m, n)) {
-        for (int i = 0; i < NBRANCH; ++i) {
-            Ctx &b = branch[i];
-            b.F = c.F;
-            b.kind = kind;
-            b.leaf = c.leaf;
-            if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess ||
-                !make_streams(b))
-                return PLUQ_ECUDA;
-            b.hw = acquire_words();
-            if (!b.hw) return PLUQ_ECUDA;
-            carve(b, L.branch, (m + 1) / 2, w);
-            PLUQ_CUDA_TRY(cudaMemsetAsync(b.d_rank, 0, 64, st));
-            b.pool = &pool;
-            pool.free.push_back(&b);
-        }
+        int i = 0;
+        for (int t = 0; t < NTIER; ++t)
+            for (int u = 0; u < TIER_COUNT[t]; ++u, ++i) {
+                Ctx &b = branch[i];
+                b.F = c.F;
+                b.kind = kind;
+                b.leaf = c.leaf;
+                b.dev = dev;
+                sbs[i] = acquire_streams();
+                if (!sbs[i]) return PLUQ_ECUDA;
+                bind(b, sbs[i], true);
+                b.hw = acquire_words();
+                if (!b.hw) return PLUQ_ECUDA;
+                b.cap_m = tier_dim(m, t);
+                b.cap_n = tier_dim(n, t);
+                carve(b, L.branch[t], b.cap_m, w);
+                PLUQ_CUDA_TRY(cudaMemsetAsync(b.d_rank, 0, 64, st));
+                b.pool = &pool;
+                pool.free.push_back(&b);
+            }
         c.pool = &pool;
     }
 
@@ -641,7 +909,17 @@ pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p
     if (flag != 0) return PLUQ_ERANGE;
 
     Res res;
+    const long long t_start = g_host_stats ? now_ns() : 0;
+    const long long w0 = g_wait_ns.load(), n0 = g_waits.load(), l0 = prof::g_launches.load();
     PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res, 0, false));
+    if (g_host_stats) {
+        cudaStreamSynchronize(st);
+        fprintf(stderr,
+                "pluq host stats: %lld x %lld: wall %.3f ms, waits %lld (%.3f ms summed over "
+                "threads), launches %lld\n",
+                (long long)m, (long long)n, (now_ns() - t_start) / 1e6, g_waits.load() - n0,
+                (g_wait_ns.load() - w0) / 1e6, prof::g_launches.load() - l0);
+    }
     if (res.pid) PLUQ_TRY(launch_iota(d_perm_p, m, st));
     if (res.qid) PLUQ_TRY(launch_iota(d_perm_q, n, st));
     PLUQ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -920,10 +1198,8 @@ pluq_status pluq_perm_rows(uint32_t *d_X, int64_t ldx, int64_t count, int64_t wi
     if (count == 0 || width == 0) return PLUQ_OK;
     if (!d_X || !d_perm || ldx < width) return PLUQ_EINVAL;
     if (!d_work || ws_bytes < (size_t)count * width * 4) return PLUQ_ENOMEM;
-    cudaStream_t st = (cudaStream_t)stream;
-    PLUQ_TRY(launch_gather(Blk{(uint32_t *)d_work, width}, d_X, ldx, count, width, d_perm, nullptr,
-                           st));
-    return launch_copy(Blk{d_X, ldx}, (uint32_t *)d_work, width, count, width, st);
+    PermOp op{d_X, ldx, count, width, d_perm, 0, true};
+    return launch_perm_ops(&op, 1, (uint32_t *)d_work, ws_bytes / 4, (cudaStream_t)stream);
 }
 
 pluq_status pluq_perm_cols(uint32_t *d_X, int64_t ldx, int64_t height, int64_t count,
@@ -933,10 +1209,8 @@ pluq_status pluq_perm_cols(uint32_t *d_X, int64_t ldx, int64_t height, int64_t c
     if (count == 0 || height == 0) return PLUQ_OK;
     if (!d_X || !d_perm || ldx < count) return PLUQ_EINVAL;
     if (!d_work || ws_bytes < (size_t)count * height * 4) return PLUQ_ENOMEM;
-    cudaStream_t st = (cudaStream_t)stream;
-    PLUQ_TRY(launch_gather(Blk{(uint32_t *)d_work, count}, d_X, ldx, height, count, nullptr,
-                           d_perm, st));
-    return launch_copy(Blk{d_X, ldx}, (uint32_t *)d_work, count, height, count, st);
+    PermOp op{d_X, ldx, height, count, d_perm, 0, false};
+    return launch_perm_ops(&op, 1, (uint32_t *)d_work, ws_bytes / 4, (cudaStream_t)stream);
 }
 
 pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p,

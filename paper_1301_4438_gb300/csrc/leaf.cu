@@ -862,10 +862,8 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     prof::start(prof::LEAF, st);
 #define PLUQ_LEAF_CASE(SP, C, R)                                                                  \
     if (small == SP && cpl == C && rpw == R) {                                                   \
-        static const bool attr = cudaFuncSetAttribute(leaf_kernel<SP, C, R>,                     \
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                      (int)smem) == cudaSuccess;                 \
-        if (!attr) return PLUQ_ECUDA;                                                            \
+        static std::atomic<uint64_t> attr{0};                                                    \
+        if (!smem_attr_once((const void *)leaf_kernel<SP, C, R>, smem, attr)) return PLUQ_ECUDA;  \
         leaf_kernel<SP, C, R><<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q,    \
                                                    info, info_len, host_info, seq,               \
                                                    try_generic ? 1 : 0);                         \

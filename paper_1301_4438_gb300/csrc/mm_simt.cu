@@ -3,7 +3,7 @@
 // triangular-inverse and TRSM code needs.
 //
 // Each product of two residues is formed exactly as a 64-bit integer and the
-// sums are reduced once per output element (the delayed reduction of Sec. 5):
+// sums are reduced once per output element (the delayed reduction of Sec. 6):
 //   p <= 2^16 : a b < 2^32, a 64-bit accumulator holds 2^32 of them;
 //   p  > 2^16 : a = a_hi 2^16 + a_lo, a_lo b < 2^47 and a_hi b < 2^46, two
 //               64-bit accumulators hold 2^17 terms each (K is cut into

@@ -20,7 +20,7 @@
 //     sets in TMEM, so the MMAs of one K-chunk run while the epilogue warps
 //     drain the previous one;
 //   * the epilogue folds each chunk into a running residue kept in registers
-//     (the delayed reduction of Sec. 5: one reduction per chunk, not per
+//     (the delayed reduction of Sec. 6: one reduction per chunk, not per
 //     product): for two limbs entirely in exact fp32 arithmetic, otherwise as
 //     one 64-bit dot product with the weights 256^s mod p and one Barrett
 //     reduction; after a tile's last chunk it applies C <- C - AB (or the
@@ -190,24 +190,46 @@ __device__ __forceinline__ void to_digits(uint32_t x, uint32_t p, __nv_bfloat16 
     d[L - 1] = __float2bfloat16_rn((float)c);
 }
 
-// One launch splits both operands.  Block rows y < Mp/32 take A (M x K, row
-// stride lda) -> planes_a[(b*L + l)*Mp + i][k]; the others take B (K x N, row
-// stride ldb) -> planes_b[(b*L + l)*Np + j][k], transposed through shared
-// memory.  Both zero padded; Np is a multiple of the tile width, not
-// necessarily of 32.
+// One launch splits both operands of every product of a group.  Each product
+// (and each entry b of its batch) is one z-slice of the grid; block rows
+// y < Mp/32 take A (M x K, row stride lda) -> planes_a[rowA + (b*L + l)*Mp + i][k],
+// the others take B (K x N, row stride ldb) -> planes_b[rowB + (b*L + l)*Np + j][k],
+// transposed through shared memory.  Both zero padded; Np is a multiple of the
+// tile width, not necessarily of 32.
+struct SplitProb {
+    const uint32_t *A, *B;
+    int64_t lda, sA, ldb, sB;
+    int M, N, batch;
+    int64_t Mp, Np, rowA, rowB;
+};
+constexpr int MAXG = 2;       // products per grouped launch
+struct SplitArgs {
+    SplitProb g[MAXG];
+    int ng, K;
+    int64_t Kp;
+    uint32_t p;
+};
+
 template <int L>
-__global__ void split_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_t sA, int M,
-                             const uint32_t *__restrict__ B, int64_t ldb, int64_t sB, int N, int K,
-                             int64_t Mp, int64_t Np, int64_t Kp, uint32_t p,
+__global__ void split_kernel(const __grid_constant__ SplitArgs sa,
                              __nv_bfloat16 *__restrict__ planes_a,
                              __nv_bfloat16 *__restrict__ planes_b)
 {
     __shared__ __nv_bfloat16 tile[L][32][33];
-    const int b = blockIdx.z;
+    int b = blockIdx.z, gi = 0;
+    while (gi < sa.ng - 1 && b >= sa.g[gi].batch) {
+        b -= sa.g[gi].batch;
+        ++gi;
+    }
+    const SplitProb &g = sa.g[gi];
+    const int M = g.M, N = g.N, K = sa.K;
+    const int64_t Mp = g.Mp, Np = g.Np, Kp = sa.Kp;
+    const uint32_t p = sa.p;
+    const uint32_t *A = g.A + b * g.sA;
+    const uint32_t *B = g.B + b * g.sB;
+    const int64_t lda = g.lda, ldb = g.ldb;
     const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int64_t ya = Mp / 32, ytot = ya + (Np + 31) / 32;
-    A += b * sA;
-    B += b * sB;
     for (int64_t by = blockIdx.y; by < ytot; by += gridDim.y) {
         if (by < ya) {
             const int64_t k = k0 + threadIdx.x;
@@ -220,7 +242,7 @@ __global__ void split_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_
                 to_digits<L>(x, p, d);
 #pragma unroll
                 for (int l = 0; l < L; ++l)
-                    planes_a[((int64_t)(b * L + l) * Mp + i) * Kp + k] = d[l];
+                    planes_a[(g.rowA + (int64_t)(b * L + l) * Mp + i) * Kp + k] = d[l];
             }
             continue;
         }
@@ -242,20 +264,30 @@ __global__ void split_kernel(const uint32_t *__restrict__ A, int64_t lda, int64_
 #pragma unroll
             for (int l = 0; l < L; ++l)
                 if (j < Np)
-                    planes_b[((int64_t)(b * L + l) * Np + j) * Kp + k] =
+                    planes_b[(g.rowB + (int64_t)(b * L + l) * Np + j) * Kp + k] =
                         tile[l][threadIdx.x][threadIdx.y + 8 * s];
         }
     }
 }
 
 // ------------------------------------------------------------- GEMM --
-struct TcArgs {
+// One product of a grouped launch (a batch of equally shaped ones); its planes
+// start at rows rowA / rowB of the stacked plane tensors.
+struct TcProb {
     uint32_t *C;
     int64_t ldc, sC;
-    int M, N, nkb;
+    int M, N;
     int Mp, Np;
-    int ntm, ntn, ntiles;      // row tiles, column tiles, tiles over the whole batch
+    int ntm, ntn;              // row and column tiles of one batch entry
+    int tiles;                 // tiles over the whole batch
+    int rowA, rowB;
     int mode;
+};
+struct TcArgs {
+    TcProb g[MAXG];
+    int ng;
+    int nkb;                   // K blocks, shared by every product of the group
+    int ntiles;                // tiles over the whole group
     Field F;
     float pf, pinv;            // p and 1/p rounded to fp32 (two-limb recombination)
     uint64_t off;              // multiple of p above the recombination bound (L != 2)
@@ -309,18 +341,25 @@ __device__ __forceinline__ uint32_t chunk_final(uint32_t run, uint32_t p)
     }
 }
 
-// Persistent tile order: GROUP_M row tiles are swept across all column tiles
-// before the next group, batch entries one after the other.
+// Persistent tile order: the products of the group one after the other, in
+// each the batch entries one after the other, in each GROUP_M row tiles swept
+// across all column tiles before the next GROUP_M.
 template <int BN>
-__device__ __forceinline__ void tile_of(int t, const TcArgs &a, int &bz, int &m0, int &n0)
+__device__ __forceinline__ void tile_of(int t, const TcArgs &a, int &gi, int &bz, int &m0, int &n0)
 {
-    const int per = a.ntm * a.ntn;
+    gi = 0;
+    while (gi < a.ng - 1 && t >= a.g[gi].tiles) {
+        t -= a.g[gi].tiles;
+        ++gi;
+    }
+    const TcProb &g = a.g[gi];
+    const int per = g.ntm * g.ntn;
     bz = t / per;
     const int r = t - bz * per;
-    const int span = GROUP_M * a.ntn;
+    const int span = GROUP_M * g.ntn;
     const int grp = r / span;
     const int first = grp * GROUP_M;
-    const int gm = min(GROUP_M, a.ntm - first);
+    const int gm = min(GROUP_M, g.ntm - first);
     const int w = r - grp * span;
     m0 = (first + w % gm) * BM;
     n0 = (w / gm) * BN;
@@ -395,8 +434,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint32_t ph = 0, issued = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-                int bz, m0, n0;
-                tile_of<BN>(t, a, bz, m0, n0);
+                int gi, bz, m0, n0;
+                tile_of<BN>(t, a, gi, bz, m0, n0);
+                const int ra = a.g[gi].rowA + bz * L * a.g[gi].Mp + m0;
+                const int rb = a.g[gi].rowB + bz * L * a.g[gi].Np + n0;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag)) {
                         ok = false;
@@ -405,10 +446,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     mbar_expect_tx(full_bar(s), G::STAGE);
 #pragma unroll
                     for (int l = 0; l < L; ++l)
-                        tma_load_2d(a_tile(s, l), &mapA, kb * BK, (bz * L + l) * a.Mp + m0, full_bar(s));
+                        tma_load_2d(a_tile(s, l), &mapA, kb * BK, ra + l * a.g[gi].Mp, full_bar(s));
 #pragma unroll
                     for (int l = 0; l < L; ++l)
-                        tma_load_2d(b_tile(s, l), &mapB, kb * BK, (bz * L + l) * a.Np + n0, full_bar(s));
+                        tma_load_2d(b_tile(s, l), &mapB, kb * BK, rb + l * a.g[gi].Np, full_bar(s));
                     ++issued;
                     if (++s == STAGES) {
                         s = 0;
@@ -496,8 +537,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         uint32_t res[CW];
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-            int bz, m0, n0;
-            tile_of<BN>(t, a, bz, m0, n0);
+            int gi, bz, m0, n0;
+            tile_of<BN>(t, a, gi, bz, m0, n0);
+            const TcProb &g = a.g[gi];
             for (int c = 0; c < nchunks; ++c, ++cc) {
                 const int buf = cc & 1;
                 if (!mbar_wait(acc_full(buf), (cc >> 1) & 1, abort_flag)) {
@@ -543,12 +585,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int col0 = n0 + half * CW;
             const int rr = lane >> 3, cq = lane & 7;
             const int grow0 = m0 + q * 32 + rr;
-            uint32_t *base = a.C + (int64_t)bz * a.sC + (int64_t)grow0 * a.ldc + col0 + cq;
-            const int64_t step = 4 * a.ldc;
-            const int rows_left = a.M - grow0;   // block row it is in range iff 4*it < rows_left
-            const int cols_left = a.N - col0 - cq;
+            uint32_t *base = g.C + (int64_t)bz * g.sC + (int64_t)grow0 * g.ldc + col0 + cq;
+            const int64_t step = 4 * g.ldc;
+            const int rows_left = g.M - grow0;   // block row it is in range iff 4*it < rows_left
+            const int cols_left = g.N - col0 - cq;
+            const int mode = g.mode;
             uint32_t cv[CW];
-            if (a.mode == MM_SUB) {
+            if (mode == MM_SUB) {
 #pragma unroll
                 for (int sl = 0; sl < CW / 8; ++sl)
 #pragma unroll
@@ -568,8 +611,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         if (4 * it < rows_left) {
                             const uint32_t v = stg[(it * 4 + rr) * 9 + cq];
                             uint32_t out;
-                            if (a.mode == MM_SUB) out = sub_mod(cv[sl * 8 + it], v, p);
-                            else if (a.mode == MM_ASSIGN) out = v;
+                            if (mode == MM_SUB) out = sub_mod(cv[sl * 8 + it], v, p);
+                            else if (mode == MM_ASSIGN) out = v;
                             else out = v == 0 ? 0u : p - v;
                             base[it * step + sl * 8] = out;
                         }
@@ -644,45 +687,82 @@ int sm_count()
 }
 
 template <int L>
-pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb, int64_t M,
-                   int64_t N, int64_t K, Field F, int mode, int64_t batch, int64_t sA, int64_t sB,
-                   int64_t sC, Arena &ar, cudaStream_t st)
+pluq_status run_tc(const MMSpec *spec, int count, int64_t K, Field F, Arena &ar, cudaStream_t st)
 {
     using G = Geo<L>;
-    const int64_t Mp = ceil_div(M, BM) * BM, Np = ceil_div(N, G::BN) * G::BN;
     const int64_t Kp = ceil_div(K, BK) * BK;
+    SplitArgs sa{};
+    TcArgs a{};
+    int64_t rowsA = 0, rowsB = 0, zsplit = 0, ysplit = 1, ntiles = 0;
+    double mm_work = 0, split_bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        const MMSpec &q = spec[i];
+        const int64_t Mp = ceil_div(q.M, BM) * BM, Np = ceil_div(q.N, G::BN) * G::BN;
+        SplitProb &sp = sa.g[i];
+        sp.A = q.A;
+        sp.B = q.B;
+        sp.lda = q.lda;
+        sp.sA = q.sA;
+        sp.ldb = q.ldb;
+        sp.sB = q.sB;
+        sp.M = (int)q.M;
+        sp.N = (int)q.N;
+        sp.batch = (int)q.batch;
+        sp.Mp = Mp;
+        sp.Np = Np;
+        sp.rowA = rowsA;
+        sp.rowB = rowsB;
+        TcProb &tp = a.g[i];
+        tp.C = q.C.ptr;
+        tp.ldc = q.C.ld;
+        tp.sC = q.sC;
+        tp.M = (int)q.M;
+        tp.N = (int)q.N;
+        tp.Mp = (int)Mp;
+        tp.Np = (int)Np;
+        tp.ntm = (int)(Mp / BM);
+        tp.ntn = (int)(Np / G::BN);
+        const int64_t tiles = (int64_t)tp.ntm * tp.ntn * q.batch;
+        if (tiles > INT32_MAX) return PLUQ_EINVAL;
+        tp.tiles = (int)tiles;
+        tp.rowA = (int)rowsA;
+        tp.rowB = (int)rowsB;
+        tp.mode = q.mode;
+        rowsA += q.batch * L * Mp;
+        rowsB += q.batch * L * Np;
+        zsplit += q.batch;
+        ysplit = std::max<int64_t>(ysplit, Mp / 32 + ceil_div(Np, 32));
+        ntiles += tiles;
+        mm_work += 2.0 * L * L * (double)q.M * q.N * K * q.batch;
+        split_bytes += (double)q.batch * ((q.M + q.N) * K * 4.0 + (Mp + Np) * Kp * 2.0 * L);
+    }
+    if (rowsA > INT32_MAX || rowsB > INT32_MAX || ntiles > INT32_MAX || zsplit > 65535)
+        return PLUQ_EINVAL;
+    sa.ng = count;
+    sa.K = (int)K;
+    sa.Kp = Kp;
+    sa.p = F.p;
     const size_t mark = ar.off;
-    auto *pa = (__nv_bfloat16 *)ar.take((size_t)batch * L * Mp * Kp * 2, 1024);
-    auto *pb = (__nv_bfloat16 *)ar.take((size_t)batch * L * Np * Kp * 2, 1024);
+    auto *pa = (__nv_bfloat16 *)ar.take((size_t)rowsA * Kp * 2, 1024);
+    auto *pb = (__nv_bfloat16 *)ar.take((size_t)rowsB * Kp * 2, 1024);
     if (!pa || !pb) return PLUQ_ENOMEM;
-    const uint32_t p = F.p;
-    dim3 blk(32, 8);
     prof::start(prof::SPLIT, st);
-    const int64_t ysplit = std::min<int64_t>(Mp / 32 + ceil_div(Np, 32), 65535);
-    split_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)ysplit, (unsigned)batch),
-                      blk, 0, st>>>(A, lda, sA, (int)M, B, ldb, sB, (int)N, (int)K, Mp, Np, Kp, p,
-                                    pa, pb);
+    split_kernel<L><<<dim3((unsigned)(Kp / 32), (unsigned)std::min<int64_t>(ysplit, 65535),
+                           (unsigned)zsplit),
+                      dim3(32, 8), 0, st>>>(sa, pa, pb);
     PLUQ_TRY(last_launch());
-    prof::stop(prof::SPLIT, st, (double)batch * ((M + N) * K * 4.0 + (Mp + Np) * Kp * 2.0 * L));
+    prof::stop(prof::SPLIT, st, split_bytes);
 
     CUtensorMap ma, mb;
-    if (!make_map(&ma, pa, batch * L * Mp, Kp, BM)) return PLUQ_ECUDA;
-    if (!make_map(&mb, pb, batch * L * Np, Kp, G::BN)) return PLUQ_ECUDA;
+    if (!make_map(&ma, pa, rowsA, Kp, BM)) return PLUQ_ECUDA;
+    if (!make_map(&mb, pb, rowsB, Kp, G::BN)) return PLUQ_ECUDA;
 
-    static const bool attr = cudaFuncSetAttribute(mm_tc_kernel<L>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)G::SMEM) == cudaSuccess;
-    if (!attr) return PLUQ_ECUDA;
-    TcArgs a;
-    a.C = C.ptr;
-    a.ldc = C.ld;
-    a.sC = sC;
-    a.M = (int)M;
-    a.N = (int)N;
+    static std::atomic<uint64_t> attr{0};
+    if (!smem_attr_once((const void *)mm_tc_kernel<L>, G::SMEM, attr)) return PLUQ_ECUDA;
+    const uint32_t p = F.p;
+    a.ng = count;
     a.nkb = (int)(Kp / BK);
-    a.Mp = (int)Mp;
-    a.Np = (int)Np;
-    a.mode = mode;
+    a.ntiles = (int)ntiles;
     a.F = F;
     a.pf = (float)p;
     a.pinv = 1.0f / (float)p;
@@ -692,17 +772,12 @@ pluq_status run_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int
         a.w[s] = (uint32_t)w;
         w = (w * 256) % p;
     }
-    a.ntm = (int)(Mp / BM);
-    a.ntn = (int)(Np / G::BN);
-    const int64_t ntiles = (int64_t)a.ntm * a.ntn * batch;
-    if (ntiles > INT32_MAX) return PLUQ_EINVAL;
-    a.ntiles = (int)ntiles;
     const int grid = (int)std::min<int64_t>(ntiles, sm_count());
     prof::start(prof::TC_MM, st);
     mm_tc_kernel<L><<<grid, NTHREADS, G::SMEM, st>>>(ma, mb, a);
     PLUQ_TRY(last_launch());
-    // algorithmic tensor work: L^2 digit products of an M x K by K x N product
-    prof::stop(prof::TC_MM, st, 2.0 * L * L * (double)M * N * K * batch);
+    // algorithmic tensor work: L^2 digit products of each M x K by K x N product
+    prof::stop(prof::TC_MM, st, mm_work);
     ar.off = mark;
     return PLUQ_OK;
 }
@@ -726,25 +801,50 @@ size_t mm_tc_workspace(int64_t M, int64_t N, int64_t K, uint32_t p, int64_t batc
     return (size_t)batch * L * (Mp + Np) * Kp * 2 + 4096;
 }
 
+size_t mm_tc_group_workspace(const MMSpec *spec, int count, int64_t K, uint32_t p)
+{
+    size_t w = 0;
+    for (int i = 0; i < count; ++i)
+        w += mm_tc_workspace(spec[i].M, spec[i].N, K, p, spec[i].batch > 0 ? spec[i].batch : 1);
+    return w;
+}
+
+pluq_status launch_mm_tc_group(const MMSpec *spec, int count, int64_t K, Field F, Arena &ar,
+                               cudaStream_t st)
+{
+    // drop empty products; K = 0 leaves SUB alone and zeroes the assign forms
+    MMSpec live[MAXG];
+    int n = 0;
+    if (count < 0 || count > MAXG) return PLUQ_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const MMSpec &q = spec[i];
+        if (q.M <= 0 || q.N <= 0 || q.batch <= 0) continue;
+        if (K == 0) {
+            if (q.mode != MM_SUB)
+                for (int64_t b = 0; b < q.batch; ++b)
+                    PLUQ_TRY(launch_zero(Blk{q.C.ptr + b * q.sC, q.C.ld}, q.M, q.N, st));
+            continue;
+        }
+        if (q.M > (1 << 30) || q.N > (1 << 30) || q.batch > 65535) return PLUQ_EINVAL;
+        live[n++] = q;
+    }
+    if (n == 0) return PLUQ_OK;
+    if (K > (1 << 30)) return PLUQ_EINVAL;
+    switch (limbs_for_prime(F.p)) {
+        case 1: return run_tc<1>(live, n, K, F, ar, st);
+        case 2: return run_tc<2>(live, n, K, F, ar, st);
+        case 3: return run_tc<3>(live, n, K, F, ar, st);
+        case 4: return run_tc<4>(live, n, K, F, ar, st);
+        default: return PLUQ_EUNSUPPORTED;
+    }
+}
+
 pluq_status launch_mm_tc(Blk C, const uint32_t *A, int64_t lda, const uint32_t *B, int64_t ldb,
                          int64_t M, int64_t N, int64_t K, Field F, int mode, int64_t batch,
                          int64_t sA, int64_t sB, int64_t sC, Arena &ar, cudaStream_t st)
 {
-    if (M <= 0 || N <= 0 || batch <= 0) return PLUQ_OK;
-    if (K == 0) {
-        if (mode == MM_SUB) return PLUQ_OK;
-        for (int64_t b = 0; b < batch; ++b)
-            PLUQ_TRY(launch_zero(Blk{C.ptr + b * sC, C.ld}, M, N, st));
-        return PLUQ_OK;
-    }
-    if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30) || batch > 65535) return PLUQ_EINVAL;
-    switch (limbs_for_prime(F.p)) {
-        case 1: return run_tc<1>(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, ar, st);
-        case 2: return run_tc<2>(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, ar, st);
-        case 3: return run_tc<3>(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, ar, st);
-        case 4: return run_tc<4>(C, A, lda, B, ldb, M, N, K, F, mode, batch, sA, sB, sC, ar, st);
-        default: return PLUQ_EUNSUPPORTED;
-    }
+    MMSpec q{C, A, lda, B, ldb, M, N, mode, batch, sA, sB, sC};
+    return launch_mm_tc_group(&q, 1, K, F, ar, st);
 }
 
 }  // namespace pluq

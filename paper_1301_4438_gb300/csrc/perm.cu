@@ -2,7 +2,9 @@
 // block permutations S and T, composition of P and Q from the four recursive
 // calls, and the rank-profile read-outs of Sec. 4.  All HBM-bound: each
 // element is read once and written once per pass, rows are walked with
-// consecutive threads on consecutive columns (coalesced), 4 columns per thread.
+// consecutive threads on consecutive 16-byte chunks (coalesced, vectorised).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace pluq {
@@ -11,20 +13,156 @@ namespace {
 constexpr int GT = 256;      // threads per block
 constexpr int GC = 4 * GT;   // columns per block
 
-__global__ void gather_kernel(uint32_t *__restrict__ dst, int64_t ldd,
-                              const uint32_t *__restrict__ src, int64_t lds, int64_t rows,
-                              int64_t cols, const int32_t *__restrict__ rmap,
-                              const int32_t *__restrict__ cmap)
+// Elements by which a row-major uint32 block sits past a 16-byte boundary;
+// chunks of four columns follow the global addresses, so column j of the
+// block lies in chunk (j + a) / 4 of its row.
+__host__ __device__ __forceinline__ int misalign(const uint32_t *X)
 {
-    const int64_t c0 = (int64_t)blockIdx.x * GC + threadIdx.x;
+    return (int)(((uintptr_t)X >> 2) & 3);
+}
+
+// dst[i][j] = src[rmap ? rmap[i] - moff : i][cmap ? cmap[j] - moff : j].
+// `a` is dst's misalignment; with `vec` (16-byte row strides, and src sharing
+// dst's misalignment unless its columns are gathered) whole chunks move as
+// uint4, the partial chunks at the ends of a row element by element.
+__global__ void move_kernel(uint32_t *__restrict__ dst, int64_t ldd, const uint32_t *__restrict__ src,
+                            int64_t lds, int64_t rows, int64_t cols, const int32_t *__restrict__ rmap,
+                            const int32_t *__restrict__ cmap, int32_t moff, int a, int vec)
+{
+    const int64_t nq = (cols + a + 3) / 4;
+    const int64_t c0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t cstep = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.y; i < rows; i += gridDim.y) {
-        const int64_t si = rmap ? rmap[i] : i;
-        const uint32_t *srow = src + si * lds;
-        uint32_t *drow = dst + i * ldd;
+        const int64_t si = rmap ? (int64_t)(rmap[i] - moff) : i;
+        const uint32_t *sr = src + si * lds;
+        uint32_t *dr = dst + i * ldd;
+        for (int64_t c = c0; c < nq; c += cstep) {
+            const int64_t j = 4 * c - a;
+            if (vec && j >= 0 && j + 4 <= cols) {
+                uint4 v;
+                if (cmap) {
+                    v.x = sr[cmap[j] - moff];
+                    v.y = sr[cmap[j + 1] - moff];
+                    v.z = sr[cmap[j + 2] - moff];
+                    v.w = sr[cmap[j + 3] - moff];
+                } else {
+                    v = *(const uint4 *)(sr + j);
+                }
+                *(uint4 *)(dr + j) = v;
+            } else {
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            int64_t j = c0 + (int64_t)s * GT;
-            if (j < cols) drow[j] = srow[cmap ? cmap[j] : j];
+                for (int e = 0; e < 4; ++e) {
+                    const int64_t jj = j + e;
+                    if (jj >= 0 && jj < cols) dr[jj] = sr[cmap ? (int64_t)(cmap[jj] - moff) : jj];
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------- in-place permutations --
+// PermR / PermC in place, in one pass, several disjoint blocks per launch.
+//  by_rows: a thread block owns a stripe of W columns (W a multiple of 4) of
+//           every row of its block, stages it in shared memory and writes row
+//           i back from staged row map[i] - moff;
+//  by cols: a thread block owns W whole rows, stages them and writes column j
+//           from staged column map[j] - moff.
+// Everything a thread block writes it has read itself first, and the stripes
+// (row groups) of a block are disjoint, so no other thread block reads what
+// it overwrites.
+struct PTask {
+    uint32_t *X;
+    int64_t ld;
+    int32_t rows, cols;
+    const int32_t *map;
+    int32_t moff;
+    int32_t by_rows;
+    int32_t W;
+    int32_t nblk;
+};
+constexpr int PT_MAX = 4;
+constexpr int PT_THREADS = 256;
+struct PTasks {
+    PTask t[PT_MAX];
+    int n;
+};
+
+__global__ void __launch_bounds__(PT_THREADS) perm_inplace_kernel(const __grid_constant__ PTasks ts)
+{
+    extern __shared__ __align__(16) uint32_t sh[];
+    int b = blockIdx.x, ti = 0;
+    while (ti < ts.n - 1 && b >= ts.t[ti].nblk) {
+        b -= ts.t[ti].nblk;
+        ++ti;
+    }
+    const PTask &t = ts.t[ti];
+    const bool vec = (t.ld & 3) == 0;
+    const int a = vec ? misalign(t.X) : 0;
+    const int rows = t.rows, cols = t.cols, W = t.W;
+    if (t.by_rows) {
+        const int c0 = b * W - a;        // first column of the stripe (chunk aligned)
+        const int nq = W / 4;
+        const int tot = rows * nq;
+        for (int q = threadIdx.x; q < tot; q += PT_THREADS) {
+            const int i = q / nq, c = q - i * nq, j = c0 + 4 * c;
+            const uint32_t *sr = t.X + (int64_t)(t.map[i] - t.moff) * t.ld;
+            uint32_t *d = sh + i * W + 4 * c;
+            if (vec && j >= 0 && j + 4 <= cols) {
+                *(uint4 *)d = *(const uint4 *)(sr + j);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j + e >= 0 && j + e < cols) d[e] = sr[j + e];
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < tot; q += PT_THREADS) {
+            const int i = q / nq, c = q - i * nq, j = c0 + 4 * c;
+            uint32_t *dr = t.X + (int64_t)i * t.ld;
+            const uint32_t *sv = sh + i * W + 4 * c;
+            if (vec && j >= 0 && j + 4 <= cols) {
+                *(uint4 *)(dr + j) = *(const uint4 *)sv;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j + e >= 0 && j + e < cols) dr[j + e] = sv[e];
+            }
+        }
+    } else {
+        const int i0 = b * W;
+        const int nr = min(W, rows - i0);
+        const int cs = (cols + a + 3) & ~3;   // staged row: element j at a + j
+        const int nq = cs / 4;
+        const int tot = nr * nq;
+        for (int q = threadIdx.x; q < tot; q += PT_THREADS) {
+            const int i = q / nq, c = q - i * nq, j = 4 * c - a;
+            const uint32_t *sr = t.X + (int64_t)(i0 + i) * t.ld;
+            uint32_t *d = sh + i * cs + 4 * c;
+            if (vec && j >= 0 && j + 4 <= cols) {
+                *(uint4 *)d = *(const uint4 *)(sr + j);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j + e >= 0 && j + e < cols) d[e] = sr[j + e];
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < tot; q += PT_THREADS) {
+            const int i = q / nq, c = q - i * nq, j = 4 * c - a;
+            uint32_t *dr = t.X + (int64_t)(i0 + i) * t.ld;
+            const uint32_t *srow = sh + i * cs + a;
+            if (vec && j >= 0 && j + 4 <= cols) {
+                uint4 v;
+                v.x = srow[t.map[j] - t.moff];
+                v.y = srow[t.map[j + 1] - t.moff];
+                v.z = srow[t.map[j + 2] - t.moff];
+                v.w = srow[t.map[j + 3] - t.moff];
+                *(uint4 *)(dr + j) = v;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (j + e >= 0 && j + e < cols) dr[j + e] = srow[t.map[j + e] - t.moff];
+            }
         }
     }
 }
@@ -251,22 +389,119 @@ dim3 grid2d(int64_t rows, int64_t cols)
 
 }  // namespace
 
-pluq_status launch_gather(Blk dst, const uint32_t *src, int64_t lds, int64_t rows, int64_t cols,
-                          const int32_t *rmap, const int32_t *cmap, cudaStream_t st)
+namespace {
+pluq_status launch_move(Blk dst, const uint32_t *src, int64_t lds, int64_t rows, int64_t cols,
+                        const int32_t *rmap, const int32_t *cmap, int32_t moff, cudaStream_t st)
 {
     if (rows <= 0 || cols <= 0) return PLUQ_OK;
+    const int a = misalign(dst.ptr);
+    const bool vec = (dst.ld & 3) == 0 && (cmap || ((lds & 3) == 0 && misalign(src) == a));
+    const int64_t nq = (cols + a + 3) / 4;
+    const int64_t gx = ceil_div(nq, GT);
+    const int64_t gy = std::min<int64_t>(rows, 65535);
     prof::start(prof::MOVE, st);
-    gather_kernel<<<grid2d(rows, cols), GT, 0, st>>>(dst.ptr, dst.ld, src, lds, rows, cols, rmap,
-                                                     cmap);
+    move_kernel<<<dim3((unsigned)gx, (unsigned)gy), GT, 0, st>>>(dst.ptr, dst.ld, src, lds, rows,
+                                                                 cols, rmap, cmap, moff, a,
+                                                                 vec ? 1 : 0);
     pluq_status s = last_launch();
     prof::stop(prof::MOVE, st, (double)rows * cols * 8.0);
     return s;
 }
 
+constexpr size_t PERM_SMEM_MAX = 200 * 1024;    // largest staging area of one thread block
+constexpr size_t PERM_SMEM_GOAL = 96 * 1024;    // preferred: two thread blocks per SM
+
+// Thread-block plan of one in-place op; false when its staging does not fit.
+bool plan_inplace(const PermOp &op, PTask &t, size_t &smem)
+{
+    if (op.rows > (1 << 30) || op.cols > (1 << 30)) return false;
+    const bool vec = (op.ld & 3) == 0;
+    const int a = vec ? misalign(op.X) : 0;
+    t.X = op.X;
+    t.ld = op.ld;
+    t.rows = (int32_t)op.rows;
+    t.cols = (int32_t)op.cols;
+    t.map = op.map;
+    t.moff = op.moff;
+    t.by_rows = op.by_rows ? 1 : 0;
+    if (op.by_rows) {
+        int W = 0;
+        for (int w : {16, 8, 4})
+            if ((size_t)op.rows * w * 4 <= PERM_SMEM_GOAL) { W = w; break; }
+        if (!W && (size_t)op.rows * 16 <= PERM_SMEM_MAX) W = 4;
+        if (!W) return false;
+        t.W = W;
+        t.nblk = (int32_t)ceil_div(op.cols + a, W);
+        smem = (size_t)op.rows * W * 4;
+    } else {
+        const size_t row_bytes = (size_t)((op.cols + a + 3) & ~3ll) * 4;
+        if (row_bytes > PERM_SMEM_MAX) return false;
+        int64_t R = (int64_t)(PERM_SMEM_GOAL / row_bytes);
+        R = std::max<int64_t>(1, std::min<int64_t>(R, 16));
+        R = std::min<int64_t>(R, op.rows);
+        t.W = (int32_t)R;
+        t.nblk = (int32_t)ceil_div(op.rows, R);
+        smem = (size_t)R * row_bytes;
+    }
+    return true;
+}
+}  // namespace
+
+pluq_status launch_gather(Blk dst, const uint32_t *src, int64_t lds, int64_t rows, int64_t cols,
+                          const int32_t *rmap, const int32_t *cmap, cudaStream_t st)
+{
+    return launch_move(dst, src, lds, rows, cols, rmap, cmap, 0, st);
+}
+
 pluq_status launch_copy(Blk dst, const uint32_t *src, int64_t lds, int64_t rows, int64_t cols,
                         cudaStream_t st)
 {
-    return launch_gather(dst, src, lds, rows, cols, nullptr, nullptr, st);
+    return launch_move(dst, src, lds, rows, cols, nullptr, nullptr, 0, st);
+}
+
+pluq_status launch_perm_ops(const PermOp *ops, int count, uint32_t *scratch, size_t scratch_elems,
+                            cudaStream_t st)
+{
+    PTasks ts{};
+    size_t smem = 0;
+    double bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        const PermOp &op = ops[i];
+        if (op.rows <= 0 || op.cols <= 0 || !op.map) continue;
+        PTask t{};
+        size_t need = 0;
+        if (ts.n < PT_MAX && plan_inplace(op, t, need)) {
+            ts.t[ts.n++] = t;
+            smem = std::max(smem, need);
+            bytes += (double)op.rows * op.cols * 8.0;
+            continue;
+        }
+        // through the scratch: gather there (with the block's misalignment, so
+        // both passes move whole chunks), then copy back
+        int a = misalign(op.X);
+        int64_t ldd = (op.cols + a + 3) & ~3ll;
+        if ((size_t)(op.rows * ldd + a) > scratch_elems) {
+            a = 0;                         // tight layout: the same moves, element by element
+            ldd = op.cols;
+        }
+        if ((size_t)(op.rows * ldd + a) > scratch_elems) return PLUQ_ENOMEM;
+        uint32_t *tmp = scratch + a;
+        PLUQ_TRY(launch_move(Blk{tmp, ldd}, op.X, op.ld, op.rows, op.cols,
+                             op.by_rows ? op.map : nullptr, op.by_rows ? nullptr : op.map, op.moff,
+                             st));
+        PLUQ_TRY(launch_move(Blk{op.X, op.ld}, tmp, ldd, op.rows, op.cols, nullptr, nullptr, 0, st));
+    }
+    if (ts.n == 0) return PLUQ_OK;
+    int64_t blocks = 0;
+    for (int i = 0; i < ts.n; ++i) blocks += ts.t[i].nblk;
+    if (blocks > INT32_MAX) return PLUQ_EINVAL;
+    static std::atomic<uint64_t> attr{0};
+    if (!smem_attr_once((const void *)perm_inplace_kernel, PERM_SMEM_MAX, attr)) return PLUQ_ECUDA;
+    prof::start(prof::MOVE, st);
+    perm_inplace_kernel<<<(unsigned)blocks, PT_THREADS, smem, st>>>(ts);
+    pluq_status s = last_launch();
+    prof::stop(prof::MOVE, st, bytes);
+    return s;
 }
 
 pluq_status launch_zero(Blk dst, int64_t rows, int64_t cols, cudaStream_t st)

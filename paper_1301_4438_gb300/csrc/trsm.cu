@@ -287,10 +287,8 @@ pluq_status launch_trsm_blocked(bool left, const uint32_t *T, int64_t ldt, Blk B
     const dim3 grid((unsigned)ceil_div(rhs, NRHS), (unsigned)nb);
 #define PLUQ_TRSM_ATTR(K, BYTES)                                                                   \
     {                                                                                             \
-        static const bool attr =                                                                  \
-            cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BYTES)) == \
-            cudaSuccess;                                                                          \
-        if (!attr) return PLUQ_ECUDA;                                                             \
+        static std::atomic<uint64_t> attr{0};                                                     \
+        if (!smem_attr_once((const void *)K, (BYTES), attr)) return PLUQ_ECUDA;                    \
     }
     if (left && blocks > 0) {
         PLUQ_TRSM_ATTR((trsm_left_blocked<SMALLP, true>), SM_LEFT)

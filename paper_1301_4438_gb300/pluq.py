@@ -78,6 +78,8 @@ _SIGS = {
                                           ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _vp]),
     "pluq_set_tuning": (ctypes.c_int, [_c_i64, _c_i64]),
     "pluq_get_tuning": (ctypes.c_int, [_i64p, _i64p]),
+    "pluq_set_branch_min": (ctypes.c_int, [_c_i64]),
+    "pluq_get_branch_min": (ctypes.c_int64, []),
     "pluq_launch_count": (ctypes.c_longlong, []),
     "pluq_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pluq_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -518,3 +520,11 @@ def pluq_get_tuning():
     b = ctypes.c_int64(0)
     _check(load().pluq_get_tuning(ctypes.byref(a), ctypes.byref(b)), "pluq_get_tuning")
     return int(a.value), int(b.value)
+
+
+def pluq_set_branch_min(branch_min: int):
+    _check(load().pluq_set_branch_min(int(branch_min)), "pluq_set_branch_min")
+
+
+def pluq_get_branch_min() -> int:
+    return int(load().pluq_get_branch_min())

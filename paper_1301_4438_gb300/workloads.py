@@ -5,7 +5,7 @@ arithmetic and imports neither the CUDA binding nor the CPU oracle, so both can
 be fed the same inputs.
 
 Matrices of a prescribed rank profile follow the paper's experimental recipe
-(Sec. 7): A = L0 . R . U0 with L0 unit lower triangular, U0 unit upper
+(Sec. 8): A = L0 . R . U0 with L0 unit lower triangular, U0 unit upper
 triangular (entries uniform in [0, p)) and R a 0/1 matrix with r ones at
 distinct rows and columns.  Left multiplication by an invertible lower
 triangular matrix and right multiplication by an invertible upper triangular
