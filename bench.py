@@ -53,8 +53,10 @@ def parse():
                     help="skip the other workloads (256^2, 4096^2, 8192x32768, batch)")
     ap.add_argument("--mm", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["pluq", "gemm", "leaf", "trsm", "perm"], default=None,
-                    help="untimed: one warm-up and one decomposition of the workload (pluq), one "
+    ap.add_argument("--profile", choices=["pluq", "planted", "gemm", "leaf", "trsm", "perm"],
+                    default=None,
+                    help="untimed: one warm-up and one decomposition of the workload (pluq) or "
+                         "of a planted --shape M,N matrix of --rank mod --p (planted), one "
                          "modular product of --shape M,N,K (gemm), one base-case call on a "
                          "uniform --shape M,N block (leaf), the left and right triangular "
                          "solves with an r x r triangle and N right-hand sides, --shape r,N "
@@ -62,7 +64,8 @@ def parse():
                          "permutations (perm), each twice, for external profilers")
     ap.add_argument("--shape", default="8192,8192,2048",
                     help="sizes for --profile gemm / leaf / trsm / perm")
-    ap.add_argument("--p", type=int, default=65521, help="modulus for --profile gemm")
+    ap.add_argument("--p", type=int, default=65521, help="modulus for --profile gemm / planted")
+    ap.add_argument("--rank", type=int, default=None, help="rank for --profile planted")
     return ap.parse_args()
 
 
@@ -106,14 +109,27 @@ def run_profile_target(args):
         for _ in range(2):
             pluq.pluq_modmm(C, A, B, p, mm=args.mm)
     else:
-        cfg = W.CONFIGS[args.workload]
+        if args.profile == "planted":
+            m, n = (int(x) for x in args.shape.split(",")[:2])
+            r = args.rank if args.rank is not None else min(m, n) // 2
+            cfg = W.Config(f"planted_{m}x{n}_r{r}", m, n, args.p, r, W.BASE_SEED + 9, "planted")
+        else:
+            cfg = W.CONFIGS[args.workload]
         A0, _ = W.make(cfg, device="cuda")
         A0 = A0.to(torch.int32)
         ws = torch.empty(pluq.pluq_workspace_size(cfg.m, cfg.n, cfg.p), dtype=torch.uint8,
                          device="cuda")
-        for _ in range(2):
+        from paper_1301_4438_gb300 import autotune
+        autotune.apply(cfg.m, cfg.n, cfg.p, deficient=cfg.kind == "planted",
+                       cache=os.path.join(ROOT, "_build_tuning.json"))
+        for it in range(2):
             A = A0.clone()
+            torch.cuda.synchronize()
+            l0 = pluq.pluq_launch_count()
             pluq.pluq_mod_p(A, cfg.p, mm=args.mm, workspace=ws)
+            torch.cuda.synchronize()
+            print(f"decomposition {it}: {pluq.pluq_launch_count() - l0} library launches",
+                  file=sys.stderr)
     torch.cuda.synchronize()
 
 
@@ -290,6 +306,7 @@ def tune_for(cfg, m, n, p):
                           cache=os.path.join(ROOT, "_build_tuning.json"), budget_s=60.0)
     pluq.pluq_set_tuning(tuned[0], tuned[1])
     pluq.pluq_set_branch_min(tuned[2])
+    pluq.pluq_set_lazy_zero_test(bool(tuned[3]))
     return tuned
 
 
@@ -321,7 +338,8 @@ def time_single(cfg, mm, steps, warmup, dev, flush):
     out = {"m": m, "n": n, "p": p, "rank": r, "mm": mm, "steps": steps, "warmup": warmup,
            "ms_per_step": ms, "value": fops(m, n, r) / (ms / 1e3) / 1e9, "unit": UNIT,
            "recipe": cfg.note,
-           "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1], "branch_min": tuned[2]}}
+           "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1], "branch_min": tuned[2],
+                      "lazy_zero_test": tuned[3]}}
     if cfg.r is not None:
         out["rank_equals_planted"] = r == cfg.r
     del A, A0, ws
@@ -606,10 +624,11 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}",
                        "rank_equals_planted": rank_ok,
                        "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1],
-                                  "branch_min": tuned[2],
+                                  "branch_min": tuned[2], "lazy_zero_test": tuned[3],
                                   "source": "autotune, one knob at a time: leaf {32,64,128}, "
                                             "small-product threshold {2^24,2^25,2^27}, "
-                                            "branch threshold {32,64,128,off}"}},
+                                            "branch threshold {32,64,128,off}, zero test "
+                                            "{awaited,lazy}"}},
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,

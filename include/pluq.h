@@ -366,6 +366,17 @@ pluq_status pluq_get_tuning(int64_t *h_leaf, int64_t *h_small_mm_macs);
 pluq_status pluq_set_branch_min(int64_t branch_min);
 int64_t pluq_get_branch_min(void);
 
+/*
+ * Before recursing into a block, the recursion tests whether the block is
+ * zero (a block's rank is the number of ones of the rank profile matrix inside
+ * it, so a zero block is finished at once: r = 0, P = Q = I).  Below a
+ * rank-deficient node, lazy = 0 waits for that test before descending; lazy =
+ * 1 descends at once and reads the answer together with the first leaf's
+ * result.  Speed only, never results.  Default 0; EINVAL unless lazy is 0 or 1.
+ */
+pluq_status pluq_set_lazy_zero_test(int lazy);
+int pluq_get_lazy_zero_test(void);
+
 /* Number of 8-bit limbs the tensor form splits residues mod p into (1 to 4). */
 int pluq_tensor_limbs(uint32_t p);
 

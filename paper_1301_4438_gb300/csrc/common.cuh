@@ -307,6 +307,12 @@ pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t 
 pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, int64_t r,
                              Field F, int kind, Arena &ar, cudaStream_t st);
 size_t trsm_workspace(int64_t r, int64_t other, uint32_t p, int kind);
+// Both solves of a node at once when both triangles are small (trsm_small_for):
+// BL (rl x N) <- L^{-1} BL and BR (M x rr) <- BR U^{-1}, one launch.
+bool trsm_small_for(int64_t r);
+pluq_status trsm_pair_small(const uint32_t *L, int64_t ldl, Blk BL, int64_t rl, int64_t N,
+                            const uint32_t *U, int64_t ldu, Blk BR, int64_t M, int64_t rr,
+                            Field F, cudaStream_t st);
 // true when a triangle of r rows is solved directly (no workspace used)
 bool trsm_direct_for(int64_t r);
 

@@ -43,6 +43,10 @@ std::atomic<int64_t> g_tune_leaf{128};
 // PLUQ(G) goes to another host thread when F and G both have at least this
 // many rows and columns (a free branch context permitting)
 std::atomic<int64_t> g_tune_branch{64};
+// zero test of a block below a rank-deficient node: false = wait for it before
+// descending (a zero block costs one round trip), true = read it with the first
+// leaf of the descent (a nonzero block costs nothing extra)
+std::atomic<bool> g_tune_lazy_zero{false};
 
 namespace {
 // byte ranges [lo, hi) spanned by a batch of strided blocks
@@ -500,7 +504,7 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     // synchronisation anyway) brings the answer along.  If the block is zero,
     // so is A1, whose decomposition then changed nothing and reported r1 = 0
     // with identity permutations.
-    const bool lazy = !eager && depth < ZDEPTH;
+    const bool lazy = (!eager || g_tune_lazy_zero.load(std::memory_order_relaxed)) && depth < ZDEPTH;
     const int32_t zseq = ++c.hw->seq;
     const int zat = ZBASE + 2 * depth;
     ++c.zero_checks;
@@ -544,7 +548,11 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     // G <- C2 - E V1: each pair is independent (disjoint outputs, shared
     // read-only operands).  The second of a pair runs on the side stream when
     // the arena has room for both scratch areas side by side.
-    {
+    if (trsm_small_for(r1)) {
+        // a small triangle: both solves in one launch
+        PLUQ_TRY(trsm_pair_small(A, lda, Blk{at(0, h), lda}, r1, n - h, A, lda, Blk{at(k, 0), lda},
+                                 m - k, r1, F, c.st));
+    } else {
         const uint32_t p = F.p;
         const size_t needL = trsm_direct_for(r1) ? 0 : trsm_workspace(r1, n - h, p, c.kind);
         const size_t needR = trsm_direct_for(r1) ? 0 : trsm_workspace(r1, m - k, p, c.kind);
@@ -810,6 +818,15 @@ pluq_status pluq_set_branch_min(int64_t branch_min)
 }
 
 int64_t pluq_get_branch_min(void) { return g_tune_branch.load(); }
+
+pluq_status pluq_set_lazy_zero_test(int lazy)
+{
+    if (lazy != 0 && lazy != 1) return PLUQ_EINVAL;
+    g_tune_lazy_zero.store(lazy != 0);
+    return PLUQ_OK;
+}
+
+int pluq_get_lazy_zero_test(void) { return g_tune_lazy_zero.load() ? 1 : 0; }
 int64_t pluq_leaf_max_rows(void) { return LEAF_MAX; }
 int64_t pluq_leaf_max_cols(void) { return LEAF_MAX; }
 

@@ -699,6 +699,29 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
         return;
     }
 
+    // A zero block (r = 0, which deep in the recursion of a rank-deficient
+    // matrix is the common case): P = Q = I and its packed form is the block
+    // itself, which phase 1 has not touched, so only the outputs are written.
+    if (r == 0) {
+        for (int i = tid; i < m; i += LT) perm_p_out[i] = i;
+        for (int j = tid; j < n; j += LT) perm_q_out[j] = j;
+        if (tid == 0) {
+            info_out[0] = 0;
+            if (info_len > 2) {
+                info_out[1] = 1;
+                info_out[2] = 1;
+            }
+            if (host_info) {
+                host_info[1] = 0;
+                host_info[2] = 1;
+                host_info[3] = 1;
+                __threadfence_system();
+                host_info[0] = seq;
+            }
+        }
+        return;
+    }
+
     // ---------------- phase 2: Algorithm 1's order of the pivots ----------
     // Pivots whose columns increase in row order are already in that order
     // (see order_pivots); otherwise thread 0 runs the quad recursion.
@@ -807,21 +830,24 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     __syncthreads();
 
     // write the packed block [L\U V; M 0] in P, Q order (phase 1's rows are in
-    // original positions, its pivots in Algorithm 1's order)
-    for (int e = tid; e < m * LM; e += LT) {
-        const int i = e / LM, j = e % LM;
-        if (j >= n) continue;
-        uint32_t v;
-        if (i < r && j >= i) {
-            const uint32_t x = S.W[S.piv_row[i] * LD + S.perm_q[j]];
-            v = mul_mod(x, S.inv_c[i], F);
-        } else if (j < r && i > j) {
-            const uint32_t x = S.W[S.perm_p[i] * LD + S.piv_col[j]];
-            v = mul_mod(x, S.inv_d[j], F);
-        } else {
-            v = 0;
+    // original positions, its pivots in Algorithm 1's order): packed row i < r
+    // is pivot row piv_row[i] over the columns perm_q, divided by c_i, from the
+    // diagonal on; packed column j < r below the diagonal is pivot column
+    // piv_col[j] over the rows perm_p, divided by d_j; the rest is zero (the
+    // rank is r).  A warp per packed row, so the branches are uniform but for
+    // the first r lanes.
+    for (int i = warp; i < m; i += NW) {
+        const bool urow = i < r;
+        const uint32_t ic = urow ? S.inv_c[i] : 0u;
+        const uint32_t *wu = S.W + (urow ? S.piv_row[i] : 0) * LD;
+        const uint32_t *wl = S.W + S.perm_p[i] * LD;
+        uint32_t *dst = A + (int64_t)i * lda;
+        for (int j = lane; j < n; j += 32) {
+            uint32_t v = 0;
+            if (urow && j >= i) v = mul_mod(wu[S.perm_q[j]], ic, F);
+            else if (j < r && i > j) v = mul_mod(wl[S.piv_col[j]], S.inv_d[j], F);
+            dst[j] = v;
         }
-        A[(int64_t)i * lda + j] = v;
     }
     for (int i = tid; i < m; i += LT) perm_p_out[i] = S.perm_p[i];
     for (int j = tid; j < n; j += LT) perm_q_out[j] = S.perm_q[j];

@@ -314,7 +314,111 @@ pluq_status trsm_direct(bool left, const uint32_t *T, int64_t ldt, Blk B, int64_
     return launch_trsm_blocked<false>(left, T, ldt, B, other, r, F, blocks, st);
 }
 
+// Triangles of order r <= RS: one thread per right-hand side, the triangle
+// in shared memory, substitution in registers with a reduction per term.
+// Thread blocks [0, nl) solve the left problem B <- L^{-1} B (thread = column
+// of B), the others the right problem B <- B U^{-1} (thread = row of B), so a
+// node's two solves D and E take one launch.
+constexpr int RS = 16;
+constexpr int ST = 128;   // threads per block of the small solver
+
+struct SmallSolve {
+    const uint32_t *T;
+    int64_t ldt;
+    uint32_t *B;
+    int64_t ldb;
+    int r;
+    int64_t other;        // number of right-hand sides
+};
+
+__global__ void __launch_bounds__(ST) trsm_small_kernel(SmallSolve ls, SmallSolve rs, int nl,
+                                                        Field F)
+{
+    __shared__ uint32_t Ts[RS][RS + 1];
+    __shared__ uint32_t dinv[RS];
+    const bool left = (int)blockIdx.x < nl;
+    const SmallSolve &t = left ? ls : rs;
+    const int r = t.r;
+    const uint32_t p = F.p;
+    for (int e = threadIdx.x; e < r * r; e += ST) {
+        const int i = e / r, c = e - (e / r) * r;
+        Ts[i][c] = t.T[(int64_t)i * t.ldt + c];
+    }
+    __syncthreads();
+    if (!left && (int)threadIdx.x < r) dinv[threadIdx.x] = inv_mod(Ts[threadIdx.x][threadIdx.x], p);
+    __syncthreads();
+    const int64_t idx = (int64_t)(left ? blockIdx.x : blockIdx.x - nl) * ST + threadIdx.x;
+    if (idx >= t.other) return;
+    uint32_t x[RS];
+    if (left) {
+        // x_i = b_i - sum_{l < i} L_il x_l
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+            if (i < r) x[i] = t.B[(int64_t)i * t.ldb + idx];
+#pragma unroll
+        for (int i = 1; i < RS; ++i) {
+            if (i >= r) break;
+            uint32_t v = x[i];
+#pragma unroll
+            for (int l = 0; l < RS; ++l)
+                if (l < i) v = sub_mod(v, mul_mod(Ts[i][l], x[l], F), p);
+            x[i] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+            if (i < r) t.B[(int64_t)i * t.ldb + idx] = x[i];
+    } else {
+        // x_j = (b_j - sum_{l < j} x_l U_lj) / U_jj
+        uint32_t *row = t.B + idx * t.ldb;
+#pragma unroll
+        for (int j = 0; j < RS; ++j)
+            if (j < r) x[j] = row[j];
+#pragma unroll
+        for (int j = 0; j < RS; ++j) {
+            if (j >= r) break;
+            uint32_t v = x[j];
+#pragma unroll
+            for (int l = 0; l < RS; ++l)
+                if (l < j) v = sub_mod(v, mul_mod(x[l], Ts[l][j], F), p);
+            x[j] = mul_mod(v, dinv[j], F);
+        }
+#pragma unroll
+        for (int j = 0; j < RS; ++j)
+            if (j < r) row[j] = x[j];
+    }
+}
+
+pluq_status launch_trsm_small(const SmallSolve *ls, const SmallSolve *rs, Field F, cudaStream_t st)
+{
+    const int64_t nl = ls ? ceil_div(ls->other, ST) : 0;
+    const int64_t nr = rs ? ceil_div(rs->other, ST) : 0;
+    if (nl + nr == 0) return PLUQ_OK;
+    if (nl + nr > INT32_MAX) return PLUQ_EINVAL;
+    const SmallSolve none{};
+    prof::start(prof::TRI, st);
+    trsm_small_kernel<<<(unsigned)(nl + nr), ST, 0, st>>>(ls ? *ls : none, rs ? *rs : none, (int)nl,
+                                                          F);
+    pluq_status s = last_launch();
+    prof::stop(prof::TRI, st,
+               (ls ? (double)ls->r * ls->r * ls->other : 0.0) +
+                   (rs ? (double)rs->r * rs->r * rs->other : 0.0));
+    return s;
+}
+
 }  // namespace
+
+bool trsm_small_for(int64_t r) { return r > 0 && r <= RS; }
+
+pluq_status trsm_pair_small(const uint32_t *L, int64_t ldl, Blk BL, int64_t rl, int64_t N,
+                            const uint32_t *U, int64_t ldu, Blk BR, int64_t M, int64_t rr,
+                            Field F, cudaStream_t st)
+{
+    SmallSolve ls{L, ldl, BL.ptr, BL.ld, (int)rl, N};
+    SmallSolve rs{U, ldu, BR.ptr, BR.ld, (int)rr, M};
+    const bool use_l = rl > 0 && N > 0, use_r = rr > 0 && M > 0;
+    if ((use_l && rl > RS) || (use_r && rr > RS)) return PLUQ_EINVAL;
+    return launch_trsm_small(use_l ? &ls : nullptr, use_r ? &rs : nullptr, F, st);
+}
 
 pluq_status tri_inv_lower_unit(const uint32_t *L, int64_t ldl, Blk X, int64_t r, Field F,
                                int kind, Arena &ar, cudaStream_t st)
@@ -415,6 +519,10 @@ pluq_status trsm_left_lower_unit(const uint32_t *L, int64_t ldl, Blk B, int64_t 
                                  Field F, int kind, Arena &ar, cudaStream_t st)
 {
     if (r <= 0 || N <= 0) return PLUQ_OK;
+    if (r <= RS) {
+        SmallSolve ls{L, ldl, B.ptr, B.ld, (int)r, N};
+        return launch_trsm_small(&ls, nullptr, F, st);
+    }
     if (r <= WR) {
         prof::start(prof::TRI, st);
         pluq_status s = trsm_direct(true, L, ldl, B, N, (int)r, F, 0, st);
@@ -442,6 +550,10 @@ pluq_status trsm_right_upper(const uint32_t *U, int64_t ldu, Blk B, int64_t M, i
                              Field F, int kind, Arena &ar, cudaStream_t st)
 {
     if (r <= 0 || M <= 0) return PLUQ_OK;
+    if (r <= RS) {
+        SmallSolve rs{U, ldu, B.ptr, B.ld, (int)r, M};
+        return launch_trsm_small(nullptr, &rs, F, st);
+    }
     if (r <= WR) {
         prof::start(prof::TRI, st);
         pluq_status s = trsm_direct(false, U, ldu, B, M, (int)r, F, 0, st);

@@ -80,6 +80,8 @@ _SIGS = {
     "pluq_get_tuning": (ctypes.c_int, [_i64p, _i64p]),
     "pluq_set_branch_min": (ctypes.c_int, [_c_i64]),
     "pluq_get_branch_min": (ctypes.c_int64, []),
+    "pluq_set_lazy_zero_test": (ctypes.c_int, [ctypes.c_int]),
+    "pluq_get_lazy_zero_test": (ctypes.c_int, []),
     "pluq_launch_count": (ctypes.c_longlong, []),
     "pluq_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pluq_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -528,3 +530,11 @@ def pluq_set_branch_min(branch_min: int):
 
 def pluq_get_branch_min() -> int:
     return int(load().pluq_get_branch_min())
+
+
+def pluq_set_lazy_zero_test(lazy: bool):
+    _check(load().pluq_set_lazy_zero_test(1 if lazy else 0), "pluq_set_lazy_zero_test")
+
+
+def pluq_get_lazy_zero_test() -> bool:
+    return bool(load().pluq_get_lazy_zero_test())

@@ -165,7 +165,8 @@ def test_modmm_strided_blocks(kind):
 @pytest.mark.parametrize("p", [3, 65521, 2147483647])
 def test_trsm_matches_oracle(kind, p):
     g = np.random.Generator(np.random.PCG64(2000 + p))
-    for (r, other) in [(1, 5), (2, 1), (31, 7), (32, 33), (63, 10), (64, 64), (65, 200), (96, 17),
+    for (r, other) in [(1, 5), (2, 1), (3, 300), (8, 129), (15, 1000), (16, 257), (17, 40),
+                       (31, 7), (32, 33), (63, 10), (64, 64), (65, 200), (96, 17),
                        (127, 9), (128, 128), (129, 20), (200, 130), (517, 300)]:
         L = g.integers(0, p, (r, r)).astype(np.uint32)
         B = g.integers(0, p, (r, other)).astype(np.uint32)
@@ -186,15 +187,40 @@ def test_trsm_matches_oracle(kind, p):
 
 def test_perm_rows_cols():
     g = np.random.Generator(np.random.PCG64(9))
-    for (h, w) in [(1, 1), (5, 1000), (1000, 3), (257, 513)]:
+    # staged in shared memory (column stripes of 16, 8 or 4 / whole rows), and
+    # the shapes past the staging limits that go through the scratch instead
+    for (h, w) in [(1, 1), (5, 1000), (1000, 3), (257, 513), (2000, 37), (5000, 21),
+                   (13000, 9), (3, 60000)]:
         X = g.integers(0, 1 << 31, (h, w)).astype(np.uint32)
         pr = g.permutation(h).astype(np.int32)
         pc = g.permutation(w).astype(np.int32)
         d = dev(X)
         pluq.pluq_perm_rows(d, torch.from_numpy(pr).cuda())
-        assert np.array_equal(host(d), X[pr])
+        assert np.array_equal(host(d), X[pr]), (h, w)
         pluq.pluq_perm_cols(d, torch.from_numpy(pc).cuda())
-        assert np.array_equal(host(d), X[pr][:, pc])
+        assert np.array_equal(host(d), X[pr][:, pc]), (h, w)
+
+
+@pytest.mark.parametrize("c0", [0, 1, 2, 3])
+@pytest.mark.parametrize("ld", [1024, 1027])
+def test_perm_strided_blocks_in_place(c0, ld):
+    """Blocks starting at every 16-byte phase, with a 16-byte row stride (whole
+    chunks move as uint4, partial chunks element by element) and without one
+    (every element on its own); nothing outside the block changes."""
+    g = np.random.Generator(np.random.PCG64(100 * c0 + ld))
+    big = g.integers(0, 1 << 31, (300, ld)).astype(np.uint32)
+    for (r0, h, w) in [(5, 257, 130), (1, 40, 700), (0, 299, 5)]:
+        pr = g.permutation(h).astype(np.int32)
+        pc = g.permutation(w).astype(np.int32)
+        d = dev(big)
+        blk = d[r0:r0 + h, c0:c0 + w]
+        pluq.pluq_perm_rows(blk, torch.from_numpy(pr).cuda())
+        want = big.copy()
+        want[r0:r0 + h, c0:c0 + w] = big[r0:r0 + h, c0:c0 + w][pr]
+        assert np.array_equal(host(d), want), ("rows", r0, h, w)
+        pluq.pluq_perm_cols(blk, torch.from_numpy(pc).cuda())
+        want[r0:r0 + h, c0:c0 + w] = want[r0:r0 + h, c0:c0 + w][:, pc]
+        assert np.array_equal(host(d), want), ("cols", r0, h, w)
 
 
 # -------------------------------------------------------- rank profiles --
