@@ -595,8 +595,53 @@ def run_ours(args):
         del Ag, Bg, Cg, wsg
         return out
 
+    # the warp-level tensor-core MMA rates of this GPU: s8 x s8 -> s32 is the
+    # integer tensor path sm_103a has (no integer tcgen05 MMA); bf16 beside it
+    s8_tops, s8_ms = pluq.measure_mma_sync_peak("s8", 500.0)
+    bf16_mma_tops, bf16_ms = pluq.measure_mma_sync_peak("bf16", 500.0)
+    peaks_mma = {"s8_mma_sync_tops": s8_tops, "bf16_mma_sync_tflops": bf16_mma_tops,
+                 "tcgen05_bf16_cublas_tflops": bf16_peak,
+                 "how": "pluq_measure_mma_sync_peak: every SM, 32 warps, 8 independent "
+                        f"accumulator chains per warp, CUDA events over {s8_ms:.0f} / "
+                        f"{bf16_ms:.0f} ms; the tcgen05 figure is MEASURED_PEAKS.json's cuBLAS "
+                        "bf16 burst"}
     gemm_big = [gemm_rate(8192, 8192, 8192, "tensor"), gemm_rate(8192, 8192, 2048, "tensor"),
                 gemm_rate(8192, 8192, 2048, "simt")]
+    # PermR / PermC of a 16384 x 16384 int32 matrix by random permutations:
+    # algorithmic bytes 8 per element (read once, written once)
+    def perm_rates(M=16384, N=16384, reps=4):
+        g = torch.Generator(device=dev)
+        g.manual_seed(3)
+        X = torch.randint(0, p, (M, N), generator=g, device=dev,
+                          dtype=torch.int64).to(torch.int32)
+        wsp = torch.empty(M * N * 4, dtype=torch.uint8, device=dev)
+        out = {"shape": [M, N], "algorithmic_bytes_per_call": 8 * M * N}
+        for name, fn, n in (("PermR", pluq.pluq_perm_rows, M), ("PermC", pluq.pluq_perm_cols, N)):
+            perms = [torch.randperm(n, generator=g, device=dev).to(torch.int32)
+                     for _ in range(reps + 1)]
+            fn(X, perms[0], workspace=wsp)
+            ms = []
+            for it in range(reps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn(X, perms[it + 1], workspace=wsp)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = statistics.mean(ms)
+            out[name] = {"ms": t, "GBps": 8.0 * M * N / (t / 1e3) / 1e9,
+                         "frac_of_hbm_peak": 8.0 * M * N / (t / 1e3) / 1e9 / hbm_peak}
+        del X, wsp
+        return out
+
+    perms_16k = perm_rates()
+    for gb in gemm_big:
+        if gb["form"] == "tensor":
+            # the same 8-bit digit products, as a fraction of what the integer
+            # mma.sync path could deliver at its measured peak
+            gb["frac_of_s8_mma_sync_peak"] = gb["tensor_TFLOPs"] / s8_tops
     del A, A0, ws, A_pinned, out_pinned
     extras = None
     if not args.no_extras:
@@ -632,6 +677,8 @@ def run_ours(args):
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,
+            "mma_peaks": peaks_mma,
+            "permutations": perms_16k,
             "kernel_classes": classes,
             "plain_cuda_core_value": simt_value,
             "other_workloads": extras,

@@ -243,9 +243,13 @@ pluq_status pluq_solve(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, 
  * Hot-path kernels of Algorithm 1, callable on their own.
  *
  * MM(C, A, B) of Sec. 2: C <- C - A B mod p (or C <- A B mod p when `assign`
- * is nonzero), A M x K, B K x N, C M x N.  C must not overlap A or B in the
- * SIMT form; the tensor form first splits A and B into limb planes held in
- * the workspace, so C may overlap B there.  Asynchronous on `stream`.
+ * is nonzero), A M x K, B K x N, C M x N.  PLUQ_MM_TENSOR runs the tensor-core
+ * kernel and PLUQ_MM_SIMT the CUDA-core one whatever the size; PLUQ_MM_AUTO
+ * sends products of at most the tuned number of multiply-adds (see
+ * pluq_set_tuning) to the CUDA cores when C overlaps neither operand, the
+ * rest to the tensor cores.  C must not overlap A or B in the SIMT form; the
+ * tensor form first splits A and B into limb planes held in the workspace, so
+ * C may overlap them there.  Asynchronous on `stream`.
  * Workspace: pluq_modmm_workspace_size.
  */
 pluq_status pluq_modmm_workspace_size(int64_t M, int64_t N, int64_t K, uint32_t p,
@@ -309,6 +313,17 @@ pluq_status pluq_leaf(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t
  *   4 limb splits (bytes), 5 triangular-inverse base blocks (field ops).
  */
 long long pluq_launch_count(void);
+
+/*
+ * Instrumentation (no counterpart in the paper): the measured rate of the
+ * warp-level tensor-core MMA on this GPU, every SM busy for about target_ms
+ * (timed with CUDA events on the legacy default stream, which it
+ * synchronises).  form 0: mma.sync m16n8k32 s8 x s8 -> s32 (the integer tensor
+ * path sm_103a offers; it has no integer tcgen05 MMA); form 1: mma.sync
+ * m16n8k16 bf16 x bf16 -> fp32.  *h_tops receives tera-operations per second
+ * (2 M N K per MMA), *h_ms the timed duration.  Errors: EINVAL, ECUDA.
+ */
+pluq_status pluq_measure_mma_sync_peak(int form, double target_ms, double *h_tops, double *h_ms);
 pluq_status pluq_profile_enable(int class_mask);
 pluq_status pluq_profile_read(int kernel_class, long long *h_launches, double *h_ms,
                               double *h_work);
@@ -376,6 +391,24 @@ int64_t pluq_get_branch_min(void);
  */
 pluq_status pluq_set_lazy_zero_test(int lazy);
 int pluq_get_lazy_zero_test(void);
+
+/*
+ * Failure detection (no counterpart in the paper).  Every wait inside a kernel
+ * that depends on other warps (the tensor-core product's pipeline barriers,
+ * the base case's step barrier) is bounded: after `tries` unsuccessful tries
+ * the kernel records an error, stops its work, lets the copies and MMAs it has
+ * issued finish (those waits keep their full bound), frees its tensor memory
+ * and returns; the block it was computing is then unspecified.
+ * pluq_set_wait_limit sets the number of tries for kernels launched
+ * afterwards: a negative value restores the built-in bounds (about 2^24 and
+ * 2^22 tries), 0 gives up before the first try (a way to exercise this path
+ * without a fault).  pluq_device_status synchronises `stream` and returns
+ * PLUQ_ETIMEOUT if any kernel of the library gave up a wait since the last
+ * call (and clears that record), else PLUQ_OK or PLUQ_ECUDA.  pluq_mod_p
+ * reports a wait given up inside it as PLUQ_ETIMEOUT itself.
+ */
+pluq_status pluq_set_wait_limit(int64_t tries);
+pluq_status pluq_device_status(void *stream);
 
 /* Number of 8-bit limbs the tensor form splits residues mod p into (1 to 4). */
 int pluq_tensor_limbs(uint32_t p);

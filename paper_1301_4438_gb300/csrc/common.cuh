@@ -263,8 +263,19 @@ pluq_status launch_mm_tc_group(const MMSpec *spec, int count, int64_t K, Field F
                                cudaStream_t st);
 size_t mm_tc_group_workspace(const MMSpec *spec, int count, int64_t K, uint32_t p);
 // Nonzero if a tensor-core kernel gave up on a bounded wait since the last
-// call (reads and clears the device word).
+// call (reads and clears the device word); likewise for the leaf's step waits.
 int tc_error_flag();
+int leaf_error_flag();
+
+// Tries of every abortable device-side wait (pluq_set_wait_limit): negative
+// keeps each kernel's built-in bound.  The waits a kernel runs while winding
+// down after giving up keep their full bound.
+extern std::atomic<int64_t> g_wait_limit;
+inline uint32_t wait_limit_or(uint32_t builtin)
+{
+    const int64_t v = g_wait_limit.load(std::memory_order_relaxed);
+    return v < 0 ? builtin : (uint32_t)(v > 0xFFFFFFFFll ? 0xFFFFFFFFll : v);
+}
 
 // Dispatch on the kind (SIMT needs C disjoint from A and B).
 pluq_status launch_mm(int kind, Blk C, const uint32_t *A, int64_t lda, const uint32_t *B,

@@ -43,6 +43,7 @@ std::atomic<int64_t> g_tune_leaf{128};
 // PLUQ(G) goes to another host thread when F and G both have at least this
 // many rows and columns (a free branch context permitting)
 std::atomic<int64_t> g_tune_branch{64};
+std::atomic<int64_t> g_wait_limit{-1};
 // zero test of a block below a rank-deficient node: false = wait for it before
 // descending (a zero block costs one round trip), true = read it with the first
 // leaf of the descent (a nonzero block costs nothing extra)
@@ -489,6 +490,7 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
         PLUQ_TRY(wait_words(c.hw, seq, c.st));
         const int32_t r = c.hw->h[1];
         ++c.leaves;
+        if (r < 0 && leaf_error_flag()) return PLUQ_ETIMEOUT;
         if (r < 0 || r > m || r > n) return PLUQ_EINTERNAL;
         out.r = r;
         out.pid = c.hw->h[2] != 0;
@@ -819,6 +821,19 @@ pluq_status pluq_set_branch_min(int64_t branch_min)
 
 int64_t pluq_get_branch_min(void) { return g_tune_branch.load(); }
 
+pluq_status pluq_set_wait_limit(int64_t tries)
+{
+    g_wait_limit.store(tries < 0 ? -1 : tries);
+    return PLUQ_OK;
+}
+
+pluq_status pluq_device_status(void *stream)
+{
+    PLUQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    const int tc = tc_error_flag(), lf = leaf_error_flag();
+    return tc || lf ? PLUQ_ETIMEOUT : PLUQ_OK;
+}
+
 pluq_status pluq_set_lazy_zero_test(int lazy)
 {
     if (lazy != 0 && lazy != 1) return PLUQ_EINVAL;
@@ -928,7 +943,16 @@ pluq_status run_one(uint32_t *d_A, int64_t m, int64_t n, int64_t lda, uint32_t p
     Res res;
     const long long t_start = g_host_stats ? now_ns() : 0;
     const long long w0 = g_wait_ns.load(), n0 = g_waits.load(), l0 = prof::g_launches.load();
-    PLUQ_TRY(rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res, 0, false));
+    {
+        const pluq_status rs = rec(c, d_A, m, n, lda, d_perm_p, d_perm_q, res, 0, false);
+        if (rs != PLUQ_OK) {
+            // a kernel that gave up a bounded wait makes later steps fail too:
+            // report the wait, and leave no record behind for the next call
+            cudaStreamSynchronize(st);
+            const int t = tc_error_flag() | leaf_error_flag();
+            return t ? PLUQ_ETIMEOUT : rs;
+        }
+    }
     if (g_host_stats) {
         cudaStreamSynchronize(st);
         fprintf(stderr,
@@ -1161,8 +1185,14 @@ pluq_status pluq_modmm(uint32_t *d_C, int64_t ldc, const uint32_t *d_A, int64_t 
     ar.size = d_work ? ws_bytes : 0;
     ar.off = 0;
     if (kind != PLUQ_MM_SIMT && ar.size < mm_tc_workspace(M, N, K, p, 1)) return PLUQ_ENOMEM;
-    return launch_mm(kind, Blk{d_C, ldc}, d_A, lda, d_B, ldb, M, N, K, make_field(p),
-                     assign ? MM_ASSIGN : MM_SUB, 1, 0, 0, 0, ar, (cudaStream_t)stream);
+    const int mode = assign ? MM_ASSIGN : MM_SUB;
+    // an explicit tensor request runs the tensor-core kernel whatever the size;
+    // AUTO sends small products to the CUDA cores as the recursion does
+    if (mm_kind == PLUQ_MM_TENSOR)
+        return launch_mm_tc(Blk{d_C, ldc}, d_A, lda, d_B, ldb, M, N, K, make_field(p), mode, 1, 0,
+                            0, 0, ar, (cudaStream_t)stream);
+    return launch_mm(kind, Blk{d_C, ldc}, d_A, lda, d_B, ldb, M, N, K, make_field(p), mode, 1, 0,
+                     0, 0, ar, (cudaStream_t)stream);
 }
 
 pluq_status pluq_trsm_workspace_size(int64_t r, int64_t other, uint32_t p, int mm_kind,

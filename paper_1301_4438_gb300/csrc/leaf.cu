@@ -258,11 +258,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Wait for phase `parity` of the step barrier (bounded; false if this or
-// another warp gave up).
-__device__ __forceinline__ bool step_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+__device__ int g_leaf_error = 0;   // set when a step wait gives up
+
+// Wait for phase `parity` of the step barrier (at most `limit` tries; false
+// if this or another warp gave up).
+__device__ __forceinline__ bool step_wait(uint32_t bar, uint32_t parity, volatile int *abort,
+                                          uint32_t limit)
 {
-    for (uint32_t it = 0; it < STEP_WAIT_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -274,6 +277,7 @@ __device__ __forceinline__ bool step_wait(uint32_t bar, uint32_t parity, volatil
         if ((it & 63) == 63 && *abort) return false;
     }
     *abort = 1;
+    atomicExch(&g_leaf_error, 1);
     return false;
 }
 constexpr int MAXC = LM / 32;  // column slots per lane for the widest block
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
                                                   int64_t lda, Field F, int32_t *perm_p_out,
                                                   int32_t *perm_q_out, int32_t *info_out,
                                                   int info_len, volatile int32_t *host_info,
-                                                  int32_t seq, int try_generic)
+                                                  int32_t seq, int try_generic, uint32_t wait_limit)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
@@ -667,7 +671,7 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
         }
-        if (!step_wait(bar, step & 1, &S.abort)) {
+        if (!step_wait(bar, step & 1, &S.abort, wait_limit)) {
             failed = true;
             break;
         }
@@ -885,6 +889,7 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     const int cpl = n <= 32 ? 1 : n <= 64 ? 2 : 4;
     const int rpw = m <= 32 ? 2 : m <= 64 ? 4 : 8;
     const bool small = F.p <= 65536u;
+    const uint32_t wlim = wait_limit_or(STEP_WAIT_LIMIT);
     prof::start(prof::LEAF, st);
 #define PLUQ_LEAF_CASE(SP, C, R)                                                                  \
     if (small == SP && cpl == C && rpw == R) {                                                   \
@@ -892,7 +897,7 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
         if (!smem_attr_once((const void *)leaf_kernel<SP, C, R>, smem, attr)) return PLUQ_ECUDA;  \
         leaf_kernel<SP, C, R><<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q,    \
                                                    info, info_len, host_info, seq,               \
-                                                   try_generic ? 1 : 0);                         \
+                                                   try_generic ? 1 : 0, wlim);                   \
     }
     PLUQ_LEAF_CASE(true, 1, 2) PLUQ_LEAF_CASE(true, 1, 4) PLUQ_LEAF_CASE(true, 1, 8)
     PLUQ_LEAF_CASE(true, 2, 2) PLUQ_LEAF_CASE(true, 2, 4) PLUQ_LEAF_CASE(true, 2, 8)
@@ -907,6 +912,14 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     const double k = (double)(m < n ? m : n);
     prof::stop(prof::LEAF, st, 2.0 * m * n * k - (double)(m + n) * k * k + 2.0 / 3.0 * k * k * k);
     return s;
+}
+
+int leaf_error_flag()
+{
+    int v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_leaf_error, sizeof(int)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(g_leaf_error, &z, sizeof(int));
+    return v;
 }
 
 }  // namespace pluq

@@ -105,10 +105,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait; false if it gave up (or another role already did)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+// bounded wait of at most `limit` tries; false if it gave up (or another role
+// already did)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort,
+                                          uint32_t limit)
 {
-    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 255) == 255 && *abort) return false;
     }
@@ -292,6 +294,7 @@ struct TcArgs {
     float pf, pinv;            // p and 1/p rounded to fp32 (two-limb recombination)
     uint64_t off;              // multiple of p above the recombination bound (L != 2)
     uint32_t w[7];             // 256^s mod p
+    uint32_t wait_limit;       // tries of each pipeline wait before the kernel gives up
 };
 
 // Chunk recombination, two limbs (257 < p < 2^17).  Every value below is an
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int ra = a.g[gi].rowA + bz * L * a.g[gi].Mp + m0;
                 const int rb = a.g[gi].rowB + bz * L * a.g[gi].Np + n0;
                 for (int kb = 0; kb < nkb; ++kb) {
-                    if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag)) {
+                    if (!mbar_wait(empty_bar(s), ph ^ 1, abort_flag, a.wait_limit)) {
                         ok = false;
                         break;
                     }
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
                 for (int c = 0; c < nchunks && ok; ++c, ++cc) {
                     const int buf = cc & 1;
-                    if (!mbar_wait(acc_empty(buf), ((cc >> 1) & 1) ^ 1, abort_flag)) {
+                    if (!mbar_wait(acc_empty(buf), ((cc >> 1) & 1) ^ 1, abort_flag, a.wait_limit)) {
                         ok = false;
                         break;
                     }
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t dacc = tmem + (uint32_t)(buf * NACC * BN);
                     const int kend = min(nkb, (c + 1) * KCB);
                     for (int kb = c * KCB; kb < kend; ++kb) {
-                        if (!mbar_wait(full_bar(s), ph, abort_flag)) {
+                        if (!mbar_wait(full_bar(s), ph, abort_flag, a.wait_limit)) {
                             ok = false;
                             break;
                         }
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const TcProb &g = a.g[gi];
             for (int c = 0; c < nchunks; ++c, ++cc) {
                 const int buf = cc & 1;
-                if (!mbar_wait(acc_full(buf), (cc >> 1) & 1, abort_flag)) {
+                if (!mbar_wait(acc_full(buf), (cc >> 1) & 1, abort_flag, a.wait_limit)) {
                     ok = false;
                     break;
                 }
@@ -761,6 +764,7 @@ pluq_status run_tc(const MMSpec *spec, int count, int64_t K, Field F, Arena &ar,
     if (!smem_attr_once((const void *)mm_tc_kernel<L>, G::SMEM, attr)) return PLUQ_ECUDA;
     const uint32_t p = F.p;
     a.ng = count;
+    a.wait_limit = wait_limit_or(WAIT_LIMIT);
     a.nkb = (int)(Kp / BK);
     a.ntiles = (int)ntiles;
     a.F = F;

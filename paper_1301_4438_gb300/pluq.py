@@ -81,8 +81,13 @@ _SIGS = {
     "pluq_set_branch_min": (ctypes.c_int, [_c_i64]),
     "pluq_get_branch_min": (ctypes.c_int64, []),
     "pluq_set_lazy_zero_test": (ctypes.c_int, [ctypes.c_int]),
+    "pluq_set_wait_limit": (ctypes.c_int, [_c_i64]),
+    "pluq_device_status": (ctypes.c_int, [_vp]),
     "pluq_get_lazy_zero_test": (ctypes.c_int, []),
     "pluq_launch_count": (ctypes.c_longlong, []),
+    "pluq_measure_mma_sync_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_double,
+                                                  ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_double)]),
     "pluq_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pluq_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_double),
@@ -538,3 +543,24 @@ def pluq_set_lazy_zero_test(lazy: bool):
 
 def pluq_get_lazy_zero_test() -> bool:
     return bool(load().pluq_get_lazy_zero_test())
+
+
+def pluq_set_wait_limit(tries: int):
+    """Tries of every abortable device-side wait (negative: built-in bounds)."""
+    _check(load().pluq_set_wait_limit(int(tries)), "pluq_set_wait_limit")
+
+
+def pluq_device_status(stream=None) -> int:
+    """Synchronise the stream; PLUQ_ETIMEOUT (-6) if a kernel gave up a wait."""
+    return int(load().pluq_device_status(_stream(stream)))
+
+
+def measure_mma_sync_peak(form: str = "s8", target_ms: float = 500.0):
+    """(tera-ops/s, ms) of mma.sync s8 x s8 -> s32 (form 's8') or bf16 -> fp32
+    ('bf16') with every SM busy for about target_ms."""
+    tops = ctypes.c_double(0)
+    ms = ctypes.c_double(0)
+    _check(load().pluq_measure_mma_sync_peak({"s8": 0, "bf16": 1}[form], float(target_ms),
+                                             ctypes.byref(tops), ctypes.byref(ms)),
+           "pluq_measure_mma_sync_peak")
+    return tops.value, ms.value

@@ -147,6 +147,35 @@ def test_pluq_equals_literal_alg1_random(p):
         assert certify(A, p, LU, pp, pq, r, exact=True) == ""
 
 
+@pytest.mark.parametrize("p", [3, 65521, 8388593, 2147483647])
+def test_pluq_equals_literal_alg1_at_leaf_size(p):
+    """The order function against the literal Algorithm 1 at the sizes the GPU
+    base case handles (64 x 64 to 128 x 128): planted profiles whose rows and
+    columns are paired at random (many descents), the anti-diagonal profile
+    (every pair of pivots a descent), dense, sparse and low-rank products."""
+    g = np.random.Generator(np.random.PCG64(4242 + p))
+    shapes = [(64, 64), (128, 128), (96, 128), (128, 100), (127, 65), (80, 113)]
+    for k, (m, n) in enumerate(shapes):
+        r = min(m, n) // 2 + k
+        cases = [W.planted(m, n, r, p, 900 + k)[0], _structured(g, m, n, p)]
+        # anti-diagonal rank profile matrix: L0 R U0 with R[i, q - 1 - i] = 1
+        q = min(m, n)
+        L0 = np.tril(g.integers(0, p, (m, m)), -1) + np.eye(m, dtype=np.int64)
+        U0 = np.triu(g.integers(0, p, (n, n)), 1) + np.eye(n, dtype=np.int64)
+        R = np.zeros((m, n), dtype=np.int64)
+        R[np.arange(q), q - 1 - np.arange(q)] = 1
+        cases.append(brute.matmul_mod(brute.matmul_mod(L0, R, p), U0, p).astype(np.uint32))
+        for A in cases:
+            LU, pp, pq, rk = oracle.pluq(A, p)
+            LU1, pp1, pq1, rk1 = oracle.pluq_alg1(A, p)
+            assert rk == rk1, (m, n)
+            assert np.array_equal(pp, pp1) and np.array_equal(pq, pq1), (m, n)
+            assert np.array_equal(LU, LU1), (m, n)
+        # the anti-diagonal case does exercise descents at every level
+        _, pp, pq, rk = oracle.pluq(cases[-1], p)
+        assert rk == q and not np.array_equal(pq[:rk], np.sort(pq[:rk]))
+
+
 @pytest.mark.parametrize("p", [2, 5, 65521])
 def test_leading_submatrix_rank_profiles(p):
     """Corollary of Lemma 2: rank profiles of every leading (k,t) submatrix are read off R."""
