@@ -190,7 +190,7 @@ def test_perm_rows_cols():
     # staged in shared memory (column stripes of 16, 8 or 4 / whole rows), and
     # the shapes past the staging limits that go through the scratch instead
     for (h, w) in [(1, 1), (5, 1000), (1000, 3), (257, 513), (2000, 37), (5000, 21),
-                   (13000, 9), (3, 60000)]:
+                   (13000, 9), (3, 60000), (4500, 1001)]:
         X = g.integers(0, 1 << 31, (h, w)).astype(np.uint32)
         pr = g.permutation(h).astype(np.int32)
         pc = g.permutation(w).astype(np.int32)
