@@ -307,6 +307,7 @@ def tune_for(cfg, m, n, p):
     pluq.pluq_set_tuning(tuned[0], tuned[1])
     pluq.pluq_set_branch_min(tuned[2])
     pluq.pluq_set_lazy_zero_test(bool(tuned[3]))
+    pluq.pluq_set_leaf_variant(bool(tuned[4]))
     return tuned
 
 
@@ -339,7 +340,7 @@ def time_single(cfg, mm, steps, warmup, dev, flush):
            "ms_per_step": ms, "value": fops(m, n, r) / (ms / 1e3) / 1e9, "unit": UNIT,
            "recipe": cfg.note,
            "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1], "branch_min": tuned[2],
-                      "lazy_zero_test": tuned[3]}}
+                      "lazy_zero_test": tuned[3], "leaf_left_looking": tuned[4]}}
     if cfg.r is not None:
         out["rank_equals_planted"] = r == cfg.r
     del A, A0, ws
@@ -637,6 +638,40 @@ def run_ours(args):
         return out
 
     perms_16k = perm_rates()
+
+    # the base case alone, right- and left-looking, on a dense 128^2 block mod
+    # 65521 (generic: blocked elimination without pivoting) and a 128^2 block of
+    # planted rank 64 mod 8388593 (rank profile, Algorithm 1's order, then
+    # elimination in that order)
+    def leaf_times(reps=20):
+        blocks = {"dense_128_p65521": (torch.from_numpy(W.uniform(128, 128, 65521, W.BASE_SEED + 21)
+                                                        .astype(np.int32)).to(dev), 65521),
+                  "planted_128_r64_p8388593": (torch.from_numpy(
+                      W.planted(128, 128, 64, 8388593, W.BASE_SEED + 22)[0].astype(np.int32))
+                      .to(dev), 8388593)}
+        old_var = pluq.pluq_get_leaf_variant()
+        out = {}
+        try:
+            for name, (B0, pb) in blocks.items():
+                for var in (False, True):
+                    pluq.pluq_set_leaf_variant(var)
+                    Bw = B0.clone()
+                    pluq.pluq_leaf(Bw, pb)
+                    # CUDA events around each base-case launch only (the call
+                    # itself also reads the rank back)
+                    pluq.pluq_profile_enable(["leaf"])
+                    for _ in range(reps):
+                        Bw.copy_(B0)
+                        pluq.pluq_leaf(Bw, pb)
+                    torch.cuda.synchronize()
+                    pluq.pluq_profile_enable(False)
+                    nl, ms, _ = pluq.pluq_profile_read("leaf")
+                    out[f"{name}:{'left' if var else 'right'}_looking_us"] = ms / nl * 1e3
+        finally:
+            pluq.pluq_set_leaf_variant(old_var)
+        return out
+
+    leaf_variants = leaf_times()
     for gb in gemm_big:
         if gb["form"] == "tensor":
             # the same 8-bit digit products, as a fraction of what the integer
@@ -670,15 +705,17 @@ def run_ours(args):
                        "rank_equals_planted": rank_ok,
                        "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1],
                                   "branch_min": tuned[2], "lazy_zero_test": tuned[3],
+                                  "leaf_left_looking": tuned[4],
                                   "source": "autotune, one knob at a time: leaf {32,64,128}, "
                                             "small-product threshold {2^24,2^25,2^27}, "
                                             "branch threshold {32,64,128,off}, zero test "
-                                            "{awaited,lazy}"}},
+                                            "{awaited,lazy}, base case {right,left}-looking"}},
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,
             "mma_peaks": peaks_mma,
             "permutations": perms_16k,
+            "base_case_variants": leaf_variants,
             "kernel_classes": classes,
             "plain_cuda_core_value": simt_value,
             "other_workloads": extras,

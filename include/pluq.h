@@ -393,6 +393,18 @@ pluq_status pluq_set_lazy_zero_test(int lazy);
 int pluq_get_lazy_zero_test(void);
 
 /*
+ * Base-case variant (Sec. 7, the remark after Algorithm 2 on a left-looking
+ * form used in the experiments): the base case's blocked elimination without
+ * pivoting is right-looking (0: each 16-column panel, once factored, updates
+ * every column to its right) or left-looking (1: a panel receives the updates
+ * of all earlier panels just before it is factored).  Both apply the same
+ * updates in the same order, so results are identical; speed only.
+ * Default 0; EINVAL unless 0 or 1.
+ */
+pluq_status pluq_set_leaf_variant(int left_looking);
+int pluq_get_leaf_variant(void);
+
+/*
  * Failure detection (no counterpart in the paper).  Every wait inside a kernel
  * that depends on other warps (the tensor-core product's pipeline barriers,
  * the base case's step barrier) is bounded: after `tries` unsuccessful tries

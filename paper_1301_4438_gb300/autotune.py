@@ -8,8 +8,9 @@ workload class (size rounded to a power of two, number of limbs of p, dense
 or rank-deficient) the tuner times `pluq_mod_p` on a seeded synthetic matrix
 of that class, one knob at a time from the defaults (leaf size, then
 small-product threshold, the size above which PLUQ(G) runs on another host
-thread, then whether zero tests below rank-deficient nodes are awaited or read
-lazily), and caches the fastest setting in a JSON file.  `apply()` looks
+thread, whether zero tests below rank-deficient nodes are awaited or read
+lazily, then the right- or left-looking base case), and caches the fastest
+setting in a JSON file.  `apply()` looks
 the class up and sets the library's process-wide knobs.
 """
 from __future__ import annotations
@@ -27,8 +28,9 @@ LEAVES = (32, 64, 128)
 SMALL_MM = (1 << 24, 1 << 25, 1 << 27)
 BRANCH = (32, 64, 128, 1 << 40)          # 2^40: never hand G to another thread
 LAZY_ZERO = (0, 1)
-DEFAULT = (128, 1 << 25, 64, 0)
-KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO)
+LEAF_LEFT = (0, 1)                       # base case right- / left-looking
+DEFAULT = (128, 1 << 25, 64, 0, 0)
+KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pluq_gb300", "tuning.json")
 
 
@@ -66,24 +68,26 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
          cache: str = DEFAULT_CACHE, budget_s: float = 60.0, force: bool = False):
     """Time the candidates on one sample of the class, one knob at a time, and
     cache the best; a class already in the cache is returned as cached unless
-    `force`.  Returns (leaf, small_mm_macs, branch_min, lazy_zero, ms)."""
+    `force`.  Returns (leaf, small_mm_macs, branch_min, lazy_zero, leaf_left, ms)."""
     key = _class_key(m, n, p, deficient)
     if not force:
         ent = _load(cache).get(key)
-        if ent and "lazy_zero" in ent:
+        if ent and "leaf_left" in ent:
             return (int(ent["leaf"]), int(ent["small_mm_macs"]), int(ent["branch_min"]),
-                    int(ent["lazy_zero"]), ent["ms"])
+                    int(ent["lazy_zero"]), int(ent["leaf_left"]), ent["ms"])
     A0 = _sample(m, n, p, deficient)
     ws = torch.empty(pluq.pluq_workspace_size(m, n, p), dtype=torch.uint8, device="cuda")
     old = pluq.pluq_get_tuning()
     old_branch = pluq.pluq_get_branch_min()
     old_lazy = pluq.pluq_get_lazy_zero_test()
+    old_left = pluq.pluq_get_leaf_variant()
     t_start = time.perf_counter()
 
     def run(cand):
         pluq.pluq_set_tuning(cand[0], cand[1])
         pluq.pluq_set_branch_min(cand[2])
         pluq.pluq_set_lazy_zero_test(bool(cand[3]))
+        pluq.pluq_set_leaf_variant(bool(cand[4]))
         times = []
         for _ in range(reps + 1):
             A = A0.clone()
@@ -111,11 +115,12 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
         pluq.pluq_set_tuning(*old)
         pluq.pluq_set_branch_min(old_branch)
         pluq.pluq_set_lazy_zero_test(old_lazy)
+        pluq.pluq_set_leaf_variant(old_left)
     data = _load(cache)
     data[key] = {"leaf": best[0], "small_mm_macs": best[1], "branch_min": best[2],
-                 "lazy_zero": best[3], "ms": best_ms}
+                 "lazy_zero": best[3], "leaf_left": best[4], "ms": best_ms}
     _store(cache, data)
-    return best[0], best[1], best[2], best[3], best_ms
+    return best[0], best[1], best[2], best[3], best[4], best_ms
 
 
 def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_CACHE) -> bool:
@@ -128,4 +133,6 @@ def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_
         pluq.pluq_set_branch_min(int(ent["branch_min"]))
     if "lazy_zero" in ent:
         pluq.pluq_set_lazy_zero_test(bool(ent["lazy_zero"]))
+    if "leaf_left" in ent:
+        pluq.pluq_set_leaf_variant(bool(ent["leaf_left"]))
     return True

@@ -354,5 +354,7 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
 // when C does not overlap A or B (launch latency dominates there).
 extern std::atomic<int64_t> g_tune_leaf;
 extern std::atomic<int64_t> g_tune_small_mm;
+// base case: right-looking (false) or left-looking (true) blocked elimination
+extern std::atomic<bool> g_tune_leaf_left;
 
 }  // namespace pluq

@@ -44,6 +44,7 @@ std::atomic<int64_t> g_tune_leaf{128};
 // many rows and columns (a free branch context permitting)
 std::atomic<int64_t> g_tune_branch{64};
 std::atomic<int64_t> g_wait_limit{-1};
+std::atomic<bool> g_tune_leaf_left{false};
 // zero test of a block below a rank-deficient node: false = wait for it before
 // descending (a zero block costs one round trip), true = read it with the first
 // leaf of the descent (a nonzero block costs nothing extra)
@@ -820,6 +821,15 @@ pluq_status pluq_set_branch_min(int64_t branch_min)
 }
 
 int64_t pluq_get_branch_min(void) { return g_tune_branch.load(); }
+
+pluq_status pluq_set_leaf_variant(int left_looking)
+{
+    if (left_looking != 0 && left_looking != 1) return PLUQ_EINVAL;
+    g_tune_leaf_left.store(left_looking != 0);
+    return PLUQ_OK;
+}
+
+int pluq_get_leaf_variant(void) { return g_tune_leaf_left.load() ? 1 : 0; }
 
 pluq_status pluq_set_wait_limit(int64_t tries)
 {

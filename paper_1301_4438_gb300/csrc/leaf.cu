@@ -394,12 +394,56 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
                            int32_t *perm_q_out, int32_t *info_out, int info_len,
                            volatile int32_t *host_info, int32_t seq,
                            const int32_t *rowmap = nullptr, const int32_t *colmap = nullptr,
-                           int kcap = -1, int pid = 1, int qid = 1)
+                           int kcap = -1, int pid = 1, int qid = 1, bool left = false)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = F.p;
     const uint32_t w16 = (uint32_t)((1ull << 16) % p);
     uint32_t *W = S.W;
+    // (3) rows [q0, q0 + bq) of columns [c0, c1) <- L_qq^{-1} of themselves
+    // (U of block q), one thread per column; (4) rows below the block, same
+    // columns, minus L_{.,q} U_q.  The right-looking form applies both to
+    // every column right of a panel as soon as it is factored; the
+    // left-looking form (the variant the base-case section mentions) defers
+    // them: a panel receives the updates of all earlier panels just before it
+    // is factored, and the columns past the last pivot at the end.  Both apply
+    // the same updates to every element in the same order.
+    auto solve_block = [&](int q0, int bq, int c0, int c1) {
+        for (int c = c0 + tid; c < c1; c += LT) {
+            uint32_t x[PB];
+#pragma unroll
+            for (int i = 0; i < PB; ++i) {
+                if (i < bq) {
+                    LAcc<SMALLP> acc;
+#pragma unroll
+                    for (int k = 0; k < PB; ++k)
+                        if (k < i) acc.add(W[(q0 + i) * LD + q0 + k], x[k]);
+                    x[i] = sub_mod(W[(q0 + i) * LD + c], acc.value(F, w16), p);
+                    W[(q0 + i) * LD + c] = x[i];
+                }
+            }
+        }
+    };
+    auto update_below = [&](int q0, int bq, int c0, int c1) {
+        for (int i = q0 + bq + warp; i < m; i += NW)
+            for (int c = c0 + lane; c < c1; c += 32) {
+                LAcc<SMALLP> acc;
+#pragma unroll
+                for (int k = 0; k < PB; ++k)
+                    if (k < bq) acc.add(W[i * LD + q0 + k], W[(q0 + k) * LD + c]);
+                W[i * LD + c] = sub_mod(W[i * LD + c], acc.value(F, w16), p);
+            }
+    };
+    // all panels before `upto` applied to columns [c0, c1)
+    auto apply_earlier = [&](int upto, int c0, int c1) {
+        for (int q0 = 0; q0 < upto; q0 += PB) {
+            const int bq = upto - q0 < PB ? upto - q0 : PB;
+            solve_block(q0, bq, c0, c1);
+            __syncthreads();
+            update_below(q0, bq, c0, c1);
+            __syncthreads();
+        }
+    };
     // asynchronous 4-byte copies: the whole block is in flight at once
     for (int i = warp; i < m; i += NW) {
         const int64_t src = rowmap ? rowmap[i] : i;
@@ -416,6 +460,7 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
     const int kmax = kcap >= 0 ? kcap : (m < n ? m : n);
     for (int j0 = 0; j0 < kmax; j0 += PB) {
         const int b = kmax - j0 < PB ? kmax - j0 : PB;
+        if (left) apply_earlier(j0, j0, j0 + b);
         const int R = m - j0;                        // panel rows
         // four lanes per panel row, four of the panel's columns each: eight rows
         // per warp, pw warps (<= 16) hold the panel
@@ -514,33 +559,15 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
         }
         __syncthreads();
         if (S.gfail) return false;
-        // (3) U12 = L11^{-1} A12 on the pivot rows, one thread per column
-        for (int c = j0 + b + tid; c < n; c += LT) {
-            uint32_t x[PB];
-#pragma unroll
-            for (int i = 0; i < PB; ++i) {
-                if (i < b) {
-                    LAcc<SMALLP> acc;
-#pragma unroll
-                    for (int k = 0; k < PB; ++k)
-                        if (k < i) acc.add(W[(j0 + i) * LD + j0 + k], x[k]);
-                    x[i] = sub_mod(W[(j0 + i) * LD + c], acc.value(F, w16), p);
-                    W[(j0 + i) * LD + c] = x[i];
-                }
-            }
+        if (!left) {
+            // (3) U12 = L11^{-1} A12 on the pivot rows; (4) A22 -= L21 U12
+            solve_block(j0, b, j0 + b, n);
+            __syncthreads();
+            update_below(j0, b, j0 + b, n);
+            __syncthreads();
         }
-        __syncthreads();
-        // (4) A22 -= L21 U12
-        for (int i = j0 + b + warp; i < m; i += NW)
-            for (int c = j0 + b + lane; c < n; c += 32) {
-                LAcc<SMALLP> acc;
-#pragma unroll
-                for (int k = 0; k < PB; ++k)
-                    if (k < b) acc.add(W[i * LD + j0 + k], W[(j0 + k) * LD + c]);
-                W[i * LD + c] = sub_mod(W[i * LD + c], acc.value(F, w16), p);
-            }
-        __syncthreads();
     }
+    if (left && kmax < n) apply_earlier(kmax, kmax, n);
     // the packed block (every entry is read into W before any is written), the
     // permutations and r
     __syncthreads();
@@ -572,7 +599,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
                                                   int64_t lda, Field F, int32_t *perm_p_out,
                                                   int32_t *perm_q_out, int32_t *info_out,
                                                   int info_len, volatile int32_t *host_info,
-                                                  int32_t seq, int try_generic, uint32_t wait_limit)
+                                                  int32_t seq, int try_generic, uint32_t wait_limit,
+                                                  int left_looking)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
@@ -580,7 +608,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     const uint32_t p = F.p;
     const Field32 F32{p, 0xFFFFFFFFu / p};
     if (try_generic && generic_lu<SMALLP>(A, m, n, lda, F, F32, S, perm_p_out, perm_q_out,
-                                          info_out, info_len, host_info, seq))
+                                          info_out, info_len, host_info, seq, nullptr, nullptr,
+                                          -1, 1, 1, left_looking != 0))
         return;
     __syncthreads();   // the generic attempt is over: S belongs to the three phases now
 
@@ -800,7 +829,8 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     if (!same) {
         __syncthreads();
         if (!generic_lu<SMALLP>(A, m, n, lda, F, F32, S, perm_p_out, perm_q_out, info_out,
-                                info_len, host_info, seq, S.perm_p, S.perm_q, r, pid, qid)) {
+                                info_len, host_info, seq, S.perm_p, S.perm_q, r, pid, qid,
+                                left_looking != 0)) {
             if (tid == 0) {
                 info_out[0] = -1;   // a zero pivot here contradicts the rank profile found
                 if (host_info) {
@@ -890,6 +920,7 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     const int rpw = m <= 32 ? 2 : m <= 64 ? 4 : 8;
     const bool small = F.p <= 65536u;
     const uint32_t wlim = wait_limit_or(STEP_WAIT_LIMIT);
+    const int lvar = g_tune_leaf_left.load(std::memory_order_relaxed) ? 1 : 0;
     prof::start(prof::LEAF, st);
 #define PLUQ_LEAF_CASE(SP, C, R)                                                                  \
     if (small == SP && cpl == C && rpw == R) {                                                   \
@@ -897,7 +928,7 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
         if (!smem_attr_once((const void *)leaf_kernel<SP, C, R>, smem, attr)) return PLUQ_ECUDA;  \
         leaf_kernel<SP, C, R><<<1, LT, smem, st>>>(A, (int)m, (int)n, lda, F, perm_p, perm_q,    \
                                                    info, info_len, host_info, seq,               \
-                                                   try_generic ? 1 : 0, wlim);                   \
+                                                   try_generic ? 1 : 0, wlim, lvar);             \
     }
     PLUQ_LEAF_CASE(true, 1, 2) PLUQ_LEAF_CASE(true, 1, 4) PLUQ_LEAF_CASE(true, 1, 8)
     PLUQ_LEAF_CASE(true, 2, 2) PLUQ_LEAF_CASE(true, 2, 4) PLUQ_LEAF_CASE(true, 2, 8)

@@ -82,6 +82,8 @@ _SIGS = {
     "pluq_get_branch_min": (ctypes.c_int64, []),
     "pluq_set_lazy_zero_test": (ctypes.c_int, [ctypes.c_int]),
     "pluq_set_wait_limit": (ctypes.c_int, [_c_i64]),
+    "pluq_set_leaf_variant": (ctypes.c_int, [ctypes.c_int]),
+    "pluq_get_leaf_variant": (ctypes.c_int, []),
     "pluq_device_status": (ctypes.c_int, [_vp]),
     "pluq_get_lazy_zero_test": (ctypes.c_int, []),
     "pluq_launch_count": (ctypes.c_longlong, []),
@@ -564,3 +566,12 @@ def measure_mma_sync_peak(form: str = "s8", target_ms: float = 500.0):
                                              ctypes.byref(tops), ctypes.byref(ms)),
            "pluq_measure_mma_sync_peak")
     return tops.value, ms.value
+
+
+def pluq_set_leaf_variant(left_looking: bool):
+    """Base case's blocked elimination: right-looking (False) or left-looking (True)."""
+    _check(load().pluq_set_leaf_variant(1 if left_looking else 0), "pluq_set_leaf_variant")
+
+
+def pluq_get_leaf_variant() -> bool:
+    return bool(load().pluq_get_leaf_variant())

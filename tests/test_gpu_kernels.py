@@ -58,6 +58,42 @@ def test_leaf_matches_oracle(p):
         assert np.array_equal(host(d), LU0), (m, n)
 
 
+@pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
+def test_leaf_left_looking_variant_matches_oracle(p):
+    """The left-looking form of the base case's blocked elimination (the
+    variant the base-case section mentions) gives the same result: generic
+    blocks (all leading minors nonzero), blocks whose generic attempt fails
+    late, rank-deficient blocks (elimination in Algorithm 1's order), wide and
+    tall ones; then a whole decomposition with it."""
+    g = np.random.Generator(np.random.PCG64(p + 31))
+    old = pluq.pluq_get_leaf_variant()
+    pluq.pluq_set_leaf_variant(True)
+    try:
+        cases = [g.integers(0, p, (128, 128)).astype(np.uint32),
+                 g.integers(0, p, (100, 128)).astype(np.uint32),
+                 g.integers(0, p, (128, 37)).astype(np.uint32),
+                 _lu_product(g, 120, 128, p, 70),
+                 W.planted(128, 128, 50, p, 5)[0],
+                 W.planted(97, 120, 97, p, 6)[0],
+                 _structured(g, 77, 66, p)]
+        for A in cases:
+            LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+            d = dev(A)
+            pp, pq, r = pluq.pluq_leaf(d, p)
+            assert r == r0, A.shape
+            assert np.array_equal(pp.cpu().numpy(), pp0), A.shape
+            assert np.array_equal(pq.cpu().numpy(), pq0), A.shape
+            assert np.array_equal(host(d), LU0), A.shape
+        A = W.planted(700, 500, 300, p, 7)[0]
+        LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+        d = dev(A)
+        pp, pq, r = pluq.pluq_mod_p(d, p)
+        assert r == r0 and np.array_equal(host(d), LU0)
+        assert np.array_equal(pp.cpu().numpy(), pp0) and np.array_equal(pq.cpu().numpy(), pq0)
+    finally:
+        pluq.pluq_set_leaf_variant(old)
+
+
 def _lu_product(g, m, n, p, zero_at):
     """L0 U0 mod p with L0 unit lower (m x m) and U0 upper (m x n) whose
     diagonal is nonzero except at `zero_at`: the leading minors are nonzero
