@@ -240,6 +240,41 @@ pluq_status pluq_solve(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, 
                        void *stream);
 
 /*
+ * CUP and PLE decompositions (Sec. 1: PLE's E = U Q is in row echelon form
+ * and its pivots are the column rank profile; CUP's C = P L is in column
+ * echelon form and its pivots are the row rank profile), from the packed
+ * result of pluq_mod_p (d_LU, r, d_perm_p, d_perm_q, not modified):
+ *   pluq_ple: A[d_perm_out[i]][.] = (L E)[i][.]; d_perm_out (m) lists the pivot
+ *     rows in increasing order of their pivot column, then the other rows
+ *     increasing; d_L (m x r, stride ldl >= r) unit lower trapezoidal; d_E
+ *     (r x n, stride lde >= n) in row echelon form, row t starting at the t-th
+ *     column of the column rank profile.
+ *   pluq_cup: A[.][d_perm_out[j]] = (C U)[.][j]; d_perm_out (n) lists the pivot
+ *     columns in increasing order of their pivot row, then the other columns
+ *     increasing; d_C (m x r, stride ldc >= r) in column echelon form, column t
+ *     starting at the t-th row of the row rank profile; d_U (r x n, stride
+ *     ldu >= n) unit upper trapezoidal.
+ * Given the permutation these factors are unique.  The paper says they follow
+ * from the PLUQ by permutations only; when Algorithm 1's pivot order is not
+ * increasing in column (row) order that is not so, and the construction adds
+ * an r x r elimination without pivoting, a triangular solve and a product
+ * (the kernels of pluq_mod_p, pluq_trsm_* and pluq_modmm, on mm_kind).
+ * Scratch: d_work of at least pluq_echelon_workspace_size(m, n, r, p,
+ * mm_kind) bytes.  Both return after the result is complete on `stream`.
+ * Errors: EINVAL, ENOTPRIME, ENOMEM, ECUDA, EINTERNAL.
+ */
+pluq_status pluq_echelon_workspace_size(int64_t m, int64_t n, int64_t r, uint32_t p, int mm_kind,
+                                        size_t *h_bytes);
+pluq_status pluq_ple(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                     const int32_t *d_perm_p, const int32_t *d_perm_q, uint32_t p,
+                     int32_t *d_perm_out, uint32_t *d_L, int64_t ldl, uint32_t *d_E, int64_t lde,
+                     int mm_kind, void *d_work, size_t ws_bytes, void *stream);
+pluq_status pluq_cup(const uint32_t *d_LU, int64_t m, int64_t n, int64_t lda, int64_t r,
+                     const int32_t *d_perm_p, const int32_t *d_perm_q, uint32_t p,
+                     int32_t *d_perm_out, uint32_t *d_C, int64_t ldc, uint32_t *d_U, int64_t ldu,
+                     int mm_kind, void *d_work, size_t ws_bytes, void *stream);
+
+/*
  * Hot-path kernels of Algorithm 1, callable on their own.
  *
  * MM(C, A, B) of Sec. 2: C <- C - A B mod p (or C <- A B mod p when `assign`

@@ -81,6 +81,11 @@ def _load():
             lib.oracle_determinant.argtypes = [_u32p, ctypes.c_int64, ctypes.c_int64,
                                                ctypes.c_uint32, _u32p]
             lib.oracle_determinant.restype = ctypes.c_int
+            for nm in ("oracle_ple", "oracle_cup"):
+                f = getattr(lib, nm)
+                f.argtypes = [_u32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                              ctypes.c_uint32, _i32p, _u32p, _u32p, _i64p]
+                f.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -306,3 +311,43 @@ def solve(A: np.ndarray, B: np.ndarray, p: int):
     X = np.zeros((n, k), dtype=np.uint32)
     X[pc, :] = Bt[:r, :]
     return X, consistent
+
+
+def ple(A: np.ndarray, p: int):
+    """PLE decomposition (Sec. 1) from its definition: returns (perm_p, L, E, r)
+    with A[perm_p] = L E, L (m x r) unit lower trapezoidal and E (r x n) in
+    row echelon form whose leading entries sit on the column rank profile."""
+    A = _u32(A)
+    m, n = A.shape
+    cap = max(min(m, n), 1)
+    pp = np.zeros(max(m, 1), dtype=np.int32)
+    L = np.zeros(max(m, 1) * cap, dtype=np.uint32)
+    E = np.zeros(cap * max(n, 1), dtype=np.uint32)
+    r = ctypes.c_int64(0)
+    z = np.zeros(1, dtype=np.uint32)
+    st = _load().oracle_ple(_ptr(A if A.size else z, _u32p), m, n, max(n, 1), p,
+                            _ptr(pp, _i32p), _ptr(L, _u32p), _ptr(E, _u32p), ctypes.byref(r))
+    if st != 0:
+        raise OracleError(st, "ple")
+    k = r.value
+    return pp[:m].copy(), L[:m * k].reshape(m, k).copy(), E[:k * n].reshape(k, n).copy(), k
+
+
+def cup(A: np.ndarray, p: int):
+    """CUP decomposition (Sec. 1) from its definition: returns (perm_q, C, U, r)
+    with A[:, perm_q] = C U, C (m x r) in column echelon form whose leading
+    entries sit on the row rank profile and U (r x n) unit upper trapezoidal."""
+    A = _u32(A)
+    m, n = A.shape
+    cap = max(min(m, n), 1)
+    pq = np.zeros(max(n, 1), dtype=np.int32)
+    C = np.zeros(max(m, 1) * cap, dtype=np.uint32)
+    U = np.zeros(cap * max(n, 1), dtype=np.uint32)
+    r = ctypes.c_int64(0)
+    z = np.zeros(1, dtype=np.uint32)
+    st = _load().oracle_cup(_ptr(A if A.size else z, _u32p), m, n, max(n, 1), p,
+                            _ptr(pq, _i32p), _ptr(C, _u32p), _ptr(U, _u32p), ctypes.byref(r))
+    if st != 0:
+        raise OracleError(st, "cup")
+    k = r.value
+    return pq[:n].copy(), C[:m * k].reshape(m, k).copy(), U[:k * n].reshape(k, n).copy(), k

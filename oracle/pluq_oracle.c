@@ -34,6 +34,9 @@
  *                            bases and particular solutions are read off it
  *                            (uses of the decomposition listed in Sec. 1)
  *   oracle_determinant       determinant by elimination with row exchanges
+ *   oracle_ple / oracle_cup  PLE and CUP decompositions from their definitions
+ *                            (Sec. 1): elimination with prescribed pivot
+ *                            positions, pivots taken from R in column (row) order
  *
  * Readings where the paper is ambiguous (all documented in the design notes):
  *   - base cases m = 1 / n = 1 bring the pivot to the front by a cyclic
@@ -718,4 +721,108 @@ int oracle_determinant(const uint32_t *A, int64_t n, int64_t lda, uint32_t p, ui
     free(W);
     *det = d;
     return O_OK;
+}
+
+/* ------------------------------------------------------------- PLE / CUP -- */
+/*
+ * PLE and CUP decompositions (Sec. 1: PLE's E is in row echelon form and its
+ * pivots give the column rank profile; CUP's C = P L is in column echelon form
+ * and its pivots give the row rank profile).  The paper gives no construction,
+ * so they are written out here from their definitions:
+ *
+ * PLE.  A = P L E with P a permutation, L (m x r) unit lower trapezoidal and E
+ * (r x n) in row echelon form whose t-th row starts at column c_t, where
+ * c_0 < c_1 < ... are the columns of the ones of the rank profile matrix R
+ * (the column rank profile) and i_t is the row of the one in column c_t.
+ * perm_p lists i_0, ..., i_{r-1}, then the other rows increasing
+ * (A[perm_p[i]][.] = (L E)[i][.]).  Given P the factors are unique: they come
+ * from elimination on P^T A with the prescribed pivot positions (t, c_t): for
+ * t = 0 .. r-1, every row below t is reduced by row t at column c_t.
+ *
+ * CUP.  A = C U Q with C (m x r) in column echelon form whose t-th column
+ * starts at row i_t (the row rank profile, increasing), U (r x n) unit upper
+ * trapezoidal and perm_q listing the columns c_t of those pivots in that
+ * order, then the other columns increasing (A[.][perm_q[j]] = (C U)[.][j]).
+ * It is the transpose of the PLE of A^T.
+ *
+ * L (ldl = r), E (lde = n), C (ldc = r), U (ldu = n) are written densely.
+ * Returns a status; *rank receives r.
+ */
+static int ple_dense(const uint32_t *A, int64_t m, int64_t n, int64_t lda, int trans, uint32_t p,
+                     int32_t *perm, uint32_t *L, uint32_t *E, int64_t *rank)
+{
+    /* the matrix worked on: A (m x n) or its transpose (n x m) */
+    const int64_t mm = trans ? n : m, nn = trans ? m : n;
+    uint32_t *M = (uint32_t *)malloc((size_t)(mm > 0 ? mm : 1) * (size_t)(nn > 0 ? nn : 1) * 4);
+    int32_t *col_of_row = (int32_t *)malloc((size_t)(mm > 0 ? mm : 1) * 4);
+    int32_t *row_of_col = (int32_t *)malloc((size_t)(nn > 0 ? nn : 1) * 4);
+    if (!M || !col_of_row || !row_of_col) { free(M); free(col_of_row); free(row_of_col); return O_ENOMEM; }
+    for (int64_t i = 0; i < mm; ++i)
+        for (int64_t j = 0; j < nn; ++j) M[i * nn + j] = trans ? A[j * lda + i] : A[i * lda + j];
+    int64_t r = oracle_rank_profile(M, mm, nn, nn > 0 ? nn : 1, p, col_of_row);
+    if (r < 0) { free(M); free(col_of_row); free(row_of_col); return (int)r; }
+    for (int64_t j = 0; j < nn; ++j) row_of_col[j] = -1;
+    for (int64_t i = 0; i < mm; ++i)
+        if (col_of_row[i] >= 0) row_of_col[col_of_row[i]] = (int32_t)i;
+    /* P: pivot rows in increasing order of their pivot column, then the rest */
+    int64_t t = 0;
+    for (int64_t j = 0; j < nn; ++j)
+        if (row_of_col[j] >= 0) perm[t++] = row_of_col[j];
+    for (int64_t i = 0; i < mm; ++i)
+        if (col_of_row[i] < 0) perm[t++] = (int32_t)i;
+    /* W = P^T M, then elimination with pivots (t, c_t) */
+    uint32_t *Wm = (uint32_t *)malloc((size_t)(mm > 0 ? mm : 1) * (size_t)(nn > 0 ? nn : 1) * 4);
+    if (!Wm) { free(M); free(col_of_row); free(row_of_col); return O_ENOMEM; }
+    for (int64_t i = 0; i < mm; ++i)
+        for (int64_t j = 0; j < nn; ++j) Wm[i * nn + j] = M[(int64_t)perm[i] * nn + j];
+    for (int64_t i = 0; i < mm; ++i)
+        for (int64_t k = 0; k < r; ++k) L[i * r + k] = (i == k) ? 1u : 0u;
+    int st = O_OK;
+    for (int64_t k = 0; k < r && st == O_OK; ++k) {
+        const int64_t c = col_of_row[perm[k]];
+        const uint32_t piv = Wm[k * nn + c];
+        if (piv == 0) { st = O_EINTERNAL; break; }
+        const uint32_t inv = inv_mod(piv, p);
+        for (int64_t i = k + 1; i < mm; ++i) {
+            const uint32_t f = mul_mod(Wm[i * nn + c], inv, p);
+            L[i * r + k] = f;
+            if (f == 0) continue;
+            for (int64_t j = 0; j < nn; ++j)
+                Wm[i * nn + j] = sub_mod(Wm[i * nn + j], mul_mod(f, Wm[k * nn + j], p), p);
+        }
+    }
+    for (int64_t k = 0; k < r; ++k)
+        for (int64_t j = 0; j < nn; ++j) E[k * nn + j] = Wm[k * nn + j];
+    for (int64_t i = r; i < mm && st == O_OK; ++i)          /* the rank is r */
+        for (int64_t j = 0; j < nn; ++j)
+            if (Wm[i * nn + j] != 0) { st = O_EINTERNAL; break; }
+    free(M); free(Wm); free(col_of_row); free(row_of_col);
+    *rank = r;
+    return st;
+}
+
+int oracle_ple(const uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+               int32_t *perm_p, uint32_t *L, uint32_t *E, int64_t *rank)
+{
+    return ple_dense(A, m, n, lda, 0, p, perm_p, L, E, rank);
+}
+
+int oracle_cup(const uint32_t *A, int64_t m, int64_t n, int64_t lda, uint32_t p,
+               int32_t *perm_q, uint32_t *C, uint32_t *U, int64_t *rank)
+{
+    /* PLE of A^T = P' L' E': C = E'^T (m x r), U = L'^T (r x n), Q = P' */
+    const int64_t cap = m < n ? m : n;
+    uint32_t *Lt = (uint32_t *)malloc((size_t)(n > 0 ? n : 1) * (size_t)(cap > 0 ? cap : 1) * 4);
+    uint32_t *Et = (uint32_t *)malloc((size_t)(cap > 0 ? cap : 1) * (size_t)(m > 0 ? m : 1) * 4);
+    if (!Lt || !Et) { free(Lt); free(Et); return O_ENOMEM; }
+    int st = ple_dense(A, m, n, lda, 1, p, perm_q, Lt, Et, rank);
+    const int64_t r = *rank;
+    if (st == O_OK) {
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t k = 0; k < r; ++k) C[i * r + k] = Et[k * m + i];
+        for (int64_t k = 0; k < r; ++k)
+            for (int64_t j = 0; j < n; ++j) U[k * n + j] = Lt[j * r + k];
+    }
+    free(Lt); free(Et);
+    return st;
 }

@@ -328,6 +328,9 @@ pluq_status trsm_pair_small(const uint32_t *L, int64_t ldl, Blk BL, int64_t rl, 
 bool trsm_direct_for(int64_t r);
 
 pluq_status launch_iota(int32_t *v, int64_t n, cudaStream_t st);
+// out_key = key[0..r) sorted (distinct keys), out_val = val in the same order
+pluq_status launch_rank_sort(const int32_t *key, const int32_t *val, int64_t r, int32_t *out_key,
+                             int32_t *out_val, cudaStream_t st);
 pluq_status launch_extract(const uint32_t *LU, int64_t lda, int64_t rows, int64_t cols,
                            uint32_t *X, int64_t ldx, bool lower, cudaStream_t st);
 pluq_status launch_leu(const uint32_t *LU, int64_t lda, int64_t m, int64_t n, int64_t r,

@@ -31,8 +31,6 @@ pluq_status launch_compose(const int32_t *p1, const int32_t *p2, const int32_t *
                            int32_t *smap, int32_t *tmap, int64_t m, int64_t n, int64_t k,
                            int64_t h, int64_t r1, int64_t r2, int64_t r3, int64_t r4,
                            cudaStream_t st);
-pluq_status launch_rank_sort(const int32_t *key, const int32_t *val, int64_t r, int32_t *out_key,
-                             int32_t *out_val, cudaStream_t st);
 pluq_status launch_check_range(const uint32_t *A, int64_t lda, int64_t m, int64_t n, uint32_t p,
                                int32_t *flag, cudaStream_t st);
 pluq_status launch_any_nonzero(const uint32_t *A, int64_t lda, int64_t m, int64_t n, int32_t *words,

@@ -76,6 +76,12 @@ _SIGS = {
     "pluq_mod_p_batched": (ctypes.c_int, [ctypes.POINTER(_vp), _i64p, _i64p, _i64p, _c_i64, _c_u32,
                                           ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64p, _vp,
                                           ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _vp]),
+    "pluq_echelon_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, _c_i64, _c_u32, ctypes.c_int,
+                                                   _szp]),
+    "pluq_ple": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp, _c_u32, _vp, _vp,
+                                _c_i64, _vp, _c_i64, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "pluq_cup": (ctypes.c_int, [_vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp, _c_u32, _vp, _vp,
+                                _c_i64, _vp, _c_i64, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "pluq_set_tuning": (ctypes.c_int, [_c_i64, _c_i64]),
     "pluq_get_tuning": (ctypes.c_int, [_i64p, _i64p]),
     "pluq_set_branch_min": (ctypes.c_int, [_c_i64]),
@@ -575,3 +581,36 @@ def pluq_set_leaf_variant(left_looking: bool):
 
 def pluq_get_leaf_variant() -> bool:
     return bool(load().pluq_get_leaf_variant())
+
+
+def _echelon(fn, LU, perm_p, perm_q, r, p, mm, stream, rows_out, left_shape, right_shape):
+    _need_cuda(LU)
+    m, n = LU.shape
+    dev = LU.device
+    size = ctypes.c_size_t(0)
+    _check(load().pluq_echelon_workspace_size(m, n, r, p, _KIND[mm], ctypes.byref(size)),
+           "pluq_echelon_workspace_size")
+    ws = torch.empty(max(size.value, 1), dtype=torch.uint8, device=dev)
+    perm = torch.empty(max(rows_out, 1), dtype=torch.int32, device=dev)
+    X = torch.zeros((max(left_shape[0], 1), max(left_shape[1], 1)), dtype=torch.int32, device=dev)
+    Y = torch.zeros((max(right_shape[0], 1), max(right_shape[1], 1)), dtype=torch.int32, device=dev)
+    _check(fn(_ptr(LU), m, n, LU.stride(0) if m else max(n, 1), r, _ptr(perm_p), _ptr(perm_q), p,
+              _ptr(perm), _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), _KIND[mm], _ptr(ws),
+              ws.numel(), _stream(stream)), fn.__name__)
+    return perm[:rows_out], X[:left_shape[0], :left_shape[1]], Y[:right_shape[0], :right_shape[1]]
+
+
+def pluq_ple(LU: torch.Tensor, perm_p: torch.Tensor, perm_q: torch.Tensor, r: int, p: int,
+             mm: str = "auto", stream=None):
+    """PLE decomposition from the packed PLUQ: returns (perm (m), L (m x r), E (r x n))
+    with A[perm] = L E, L unit lower trapezoidal, E in row echelon form."""
+    m, n = LU.shape
+    return _echelon(load().pluq_ple, LU, perm_p, perm_q, r, p, mm, stream, m, (m, r), (r, n))
+
+
+def pluq_cup(LU: torch.Tensor, perm_p: torch.Tensor, perm_q: torch.Tensor, r: int, p: int,
+             mm: str = "auto", stream=None):
+    """CUP decomposition from the packed PLUQ: returns (perm (n), C (m x r), U (r x n))
+    with A[:, perm] = C U, C in column echelon form, U unit upper trapezoidal."""
+    m, n = LU.shape
+    return _echelon(load().pluq_cup, LU, perm_p, perm_q, r, p, mm, stream, n, (m, r), (r, n))

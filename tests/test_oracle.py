@@ -632,3 +632,101 @@ def test_use_pins_reject_plausible_mistakes():
     other = (X[:, 0].astype(np.int64) + N[:, 0]) % p
     assert not np.any(brute.matmul_mod(A, other[:, None], p) - b.astype(np.int64))
     assert np.any(other[free])
+
+
+# ------------------------------------------------------------ PLE / CUP --
+# Sec. 1 relates the PLUQ to the PLE (E in row echelon form, pivots on the
+# column rank profile) and CUP (C in column echelon form, pivots on the row
+# rank profile) decompositions.  The oracle writes them out from their
+# definitions; these pins check every defining property against brute force.
+
+def _greedy_profiles(A, p):
+    """Row and column rank profiles by greedy rank tests (brute force)."""
+    A = A.astype(np.int64)
+    m, n = A.shape
+    rows, cols = [], []
+    for i in range(m):
+        if brute.batch_rank(A[rows + [i]][None], p)[0] > len(rows):
+            rows.append(i)
+    for j in range(n):
+        if brute.batch_rank(A[:, cols + [j]][None], p)[0] > len(cols):
+            cols.append(j)
+    return rows, cols
+
+
+def _leading(v):
+    nz = np.nonzero(v)[0]
+    return int(nz[0]) if nz.size else -1
+
+
+@pytest.mark.parametrize("p", [2, 3, 7, 65521, 2147483647])
+def test_ple_cup_defining_properties(p):
+    g = np.random.Generator(np.random.PCG64(777 + p))
+    shapes = [(1, 1), (2, 5), (5, 2), (6, 6), (9, 7), (7, 12), (16, 16), (0, 4), (4, 0)]
+    for (m, n) in shapes:
+        for _ in range(3):
+            A = _structured(g, m, n, p) if m and n else np.zeros((m, n), np.uint32)
+            rows, cols = _greedy_profiles(A, p) if m and n else ([], [])
+            r = len(rows)
+            # PLE: A[P] = L E
+            pp, L, E, rk = oracle.ple(A, p)
+            assert rk == r
+            assert sorted(pp.tolist()) == list(range(m))
+            prod = brute.matmul_mod(L, E, p) if r else np.zeros((m, n), np.int64)
+            assert np.array_equal(prod, A[pp].astype(np.int64))
+            assert np.array_equal(np.triu(L, 1), np.zeros_like(L)) and all(L[t, t] == 1 for t in range(r))
+            lead = [_leading(E[t]) for t in range(r)]
+            assert lead == cols                      # row echelon on the column rank profile
+            # CUP: A[:, Q] = C U
+            pq, C, U, rk2 = oracle.cup(A, p)
+            assert rk2 == r
+            assert sorted(pq.tolist()) == list(range(n))
+            prod = brute.matmul_mod(C, U, p) if r else np.zeros((m, n), np.int64)
+            assert np.array_equal(prod, A[:, pq].astype(np.int64))
+            assert np.array_equal(np.tril(U, -1), np.zeros_like(U)) and all(U[t, t] == 1 for t in range(r))
+            lead_c = [_leading(C[:, t]) for t in range(r)]
+            assert lead_c == rows                    # column echelon on the row rank profile
+            # the pivot rows / columns come first, the others after in increasing order
+            assert pp[r:].tolist() == sorted(set(range(m)) - set(pp[:r].tolist()))
+            assert pq[r:].tolist() == sorted(set(range(n)) - set(pq[:r].tolist()))
+
+
+def test_ple_cup_closed_form_2x2():
+    """A = [[0, a], [b, c]] (a, b nonzero): the pivots (0, 1) and (1, 0) form a
+    descent.  PLE: P swaps the rows, L = I, E = [[b, c], [0, a]].  CUP: Q swaps
+    the columns, C = [[a, 0], [c, b]], U = I."""
+    p = 65521
+    g = np.random.Generator(np.random.PCG64(5))
+    for _ in range(20):
+        a, b = (int(x) for x in g.integers(1, p, 2))
+        c = int(g.integers(0, p))
+        A = np.array([[0, a], [b, c]], dtype=np.uint32)
+        pp, L, E, r = oracle.ple(A, p)
+        assert r == 2 and pp.tolist() == [1, 0]
+        assert L.tolist() == [[1, 0], [0, 1]] and E.tolist() == [[b, c], [0, a]]
+        pq, C, U, r = oracle.cup(A, p)
+        assert r == 2 and pq.tolist() == [1, 0]
+        assert C.tolist() == [[a, 0], [c, b]] and U.tolist() == [[1, 0], [0, 1]]
+
+
+def test_ple_needs_more_than_permuting_the_pluq_factors():
+    """The reading behind the GPU construction: Sec. 1 says a PLE follows from
+    the PLUQ by permutations only.  On the 2x2 example with a descent, the
+    rank-one terms of A = P [L; M] [U V] Q sorted by pivot column give a left
+    factor that no row permutation bringing the pivot rows to the diagonal
+    makes lower triangular, so the L of the PLE is not a permutation of the
+    PLUQ's L (an r x r elimination without pivoting is needed)."""
+    p = 65521
+    A = np.array([[0, 3], [5, 2]], dtype=np.uint32)
+    LU, pp, pq, r = oracle.pluq(A, p)
+    assert r == 2 and pp.tolist() == [0, 1] and pq.tolist() == [1, 0]   # pivots (0,1), (1,0)
+    Lp = np.tril(LU.astype(np.int64), -1) + np.eye(2, dtype=np.int64)    # [L; M] in packed order
+    Lbar = np.zeros((2, 2), dtype=np.int64)
+    Lbar[np.ix_(pp, pp)] = Lp                                             # P [L 0; M I] P^T
+    order = np.argsort(pq[:r])                                            # pivots by column
+    Lc = Lbar[:, pp[:r][order]]
+    assert Lc[0, 1] != 0                          # (0,1) lies above the diagonal in any row order
+    Pt = Lc[pp[:r][order]]                        # the row order that puts pivot rows on the diagonal
+    assert not np.array_equal(np.triu(Pt, 1), np.zeros_like(Pt))
+    _, L, _, _ = oracle.ple(A, p)
+    assert L.tolist() == [[1, 0], [0, 1]]
