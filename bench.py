@@ -308,6 +308,7 @@ def tune_for(cfg, m, n, p):
     pluq.pluq_set_branch_min(tuned[2])
     pluq.pluq_set_lazy_zero_test(bool(tuned[3]))
     pluq.pluq_set_leaf_variant(bool(tuned[4]))
+    pluq.pluq_set_node_kernel(bool(tuned[5]))
     return tuned
 
 
@@ -340,7 +341,8 @@ def time_single(cfg, mm, steps, warmup, dev, flush):
            "ms_per_step": ms, "value": fops(m, n, r) / (ms / 1e3) / 1e9, "unit": UNIT,
            "recipe": cfg.note,
            "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1], "branch_min": tuned[2],
-                      "lazy_zero_test": tuned[3], "leaf_left_looking": tuned[4]}}
+                      "lazy_zero_test": tuned[3], "leaf_left_looking": tuned[4],
+                      "node_kernel": tuned[5]}}
     if cfg.r is not None:
         out["rank_equals_planted"] = r == cfg.r
     del A, A0, ws
@@ -705,11 +707,12 @@ def run_ours(args):
                        "rank_equals_planted": rank_ok,
                        "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1],
                                   "branch_min": tuned[2], "lazy_zero_test": tuned[3],
-                                  "leaf_left_looking": tuned[4],
+                                  "leaf_left_looking": tuned[4], "node_kernel": tuned[5],
                                   "source": "autotune, one knob at a time: leaf {32,64,128}, "
                                             "small-product threshold {2^24,2^25,2^27}, "
                                             "branch threshold {32,64,128,off}, zero test "
-                                            "{awaited,lazy}, base case {right,left}-looking"}},
+                                            "{awaited,lazy}, base case {right,left}-looking, "
+                                            "node kernel {on,off}"}},
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,

@@ -440,6 +440,19 @@ pluq_status pluq_set_leaf_variant(int left_looking);
 int pluq_get_leaf_variant(void);
 
 /*
+ * Node kernel (speed only, never results): below a rank-deficient node of
+ * the recursion, a node whose four blocks A1, F, G, R are all base cases
+ * (both sides at most twice the leaf size) is computed by one thread block in
+ * one launch -- the four base cases and the permutations, triangular solves
+ * and products of Algorithm 1's step between them -- instead of a dozen
+ * launches and four host round trips.  It pays where those blocks hold few
+ * pivots, deep in a rank-deficient matrix.  1 enables it (the default), 0
+ * keeps every node on the host-driven path.  EINVAL unless 0 or 1.
+ */
+pluq_status pluq_set_node_kernel(int on);
+int pluq_get_node_kernel(void);
+
+/*
  * Failure detection (no counterpart in the paper).  Every wait inside a kernel
  * that depends on other warps (the tensor-core product's pipeline barriers,
  * the base case's step barrier) is bounded: after `tries` unsuccessful tries

@@ -9,8 +9,9 @@ or rank-deficient) the tuner times `pluq_mod_p` on a seeded synthetic matrix
 of that class, one knob at a time from the defaults (leaf size, then
 small-product threshold, the size above which PLUQ(G) runs on another host
 thread, whether zero tests below rank-deficient nodes are awaited or read
-lazily, then the right- or left-looking base case), and caches the fastest
-setting in a JSON file.  `apply()` looks
+lazily, the right- or left-looking base case, then whether small nodes below
+rank-deficient ones run in one thread block), and caches the fastest setting
+in a JSON file.  `apply()` looks
 the class up and sets the library's process-wide knobs.
 """
 from __future__ import annotations
@@ -29,8 +30,9 @@ SMALL_MM = (1 << 24, 1 << 25, 1 << 27)
 BRANCH = (32, 64, 128, 1 << 40)          # 2^40: never hand G to another thread
 LAZY_ZERO = (0, 1)
 LEAF_LEFT = (0, 1)                       # base case right- / left-looking
-DEFAULT = (128, 1 << 25, 64, 0, 0)
-KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT)
+NODE = (1, 0)                            # small deficient nodes in one thread block
+DEFAULT = (128, 1 << 25, 64, 0, 0, 1)
+KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT, NODE)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pluq_gb300", "tuning.json")
 
 
@@ -68,19 +70,20 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
          cache: str = DEFAULT_CACHE, budget_s: float = 60.0, force: bool = False):
     """Time the candidates on one sample of the class, one knob at a time, and
     cache the best; a class already in the cache is returned as cached unless
-    `force`.  Returns (leaf, small_mm_macs, branch_min, lazy_zero, leaf_left, ms)."""
+    `force`.  Returns (leaf, small_mm_macs, branch_min, lazy_zero, leaf_left, node, ms)."""
     key = _class_key(m, n, p, deficient)
     if not force:
         ent = _load(cache).get(key)
-        if ent and "leaf_left" in ent:
+        if ent and "node" in ent:
             return (int(ent["leaf"]), int(ent["small_mm_macs"]), int(ent["branch_min"]),
-                    int(ent["lazy_zero"]), int(ent["leaf_left"]), ent["ms"])
+                    int(ent["lazy_zero"]), int(ent["leaf_left"]), int(ent["node"]), ent["ms"])
     A0 = _sample(m, n, p, deficient)
     ws = torch.empty(pluq.pluq_workspace_size(m, n, p), dtype=torch.uint8, device="cuda")
     old = pluq.pluq_get_tuning()
     old_branch = pluq.pluq_get_branch_min()
     old_lazy = pluq.pluq_get_lazy_zero_test()
     old_left = pluq.pluq_get_leaf_variant()
+    old_node = pluq.pluq_get_node_kernel()
     t_start = time.perf_counter()
 
     def run(cand):
@@ -88,6 +91,7 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
         pluq.pluq_set_branch_min(cand[2])
         pluq.pluq_set_lazy_zero_test(bool(cand[3]))
         pluq.pluq_set_leaf_variant(bool(cand[4]))
+        pluq.pluq_set_node_kernel(bool(cand[5]))
         times = []
         for _ in range(reps + 1):
             A = A0.clone()
@@ -116,11 +120,12 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
         pluq.pluq_set_branch_min(old_branch)
         pluq.pluq_set_lazy_zero_test(old_lazy)
         pluq.pluq_set_leaf_variant(old_left)
+        pluq.pluq_set_node_kernel(old_node)
     data = _load(cache)
     data[key] = {"leaf": best[0], "small_mm_macs": best[1], "branch_min": best[2],
-                 "lazy_zero": best[3], "leaf_left": best[4], "ms": best_ms}
+                 "lazy_zero": best[3], "leaf_left": best[4], "node": best[5], "ms": best_ms}
     _store(cache, data)
-    return best[0], best[1], best[2], best[3], best[4], best_ms
+    return best[0], best[1], best[2], best[3], best[4], best[5], best_ms
 
 
 def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_CACHE) -> bool:
@@ -135,4 +140,6 @@ def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_
         pluq.pluq_set_lazy_zero_test(bool(ent["lazy_zero"]))
     if "leaf_left" in ent:
         pluq.pluq_set_leaf_variant(bool(ent["leaf_left"]))
+    if "node" in ent:
+        pluq.pluq_set_node_kernel(bool(ent["node"]))
     return True

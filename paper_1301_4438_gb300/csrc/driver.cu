@@ -43,6 +43,7 @@ std::atomic<int64_t> g_tune_leaf{128};
 std::atomic<int64_t> g_tune_branch{64};
 std::atomic<int64_t> g_wait_limit{-1};
 std::atomic<bool> g_tune_leaf_left{false};
+std::atomic<bool> g_tune_node{true};
 // zero test of a block below a rank-deficient node: false = wait for it before
 // descending (a zero block costs one round trip), true = read it with the first
 // leaf of the descent (a nonzero block costs nothing extra)
@@ -496,6 +497,23 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
         out.qid = c.hw->h[3] != 0;
         return PLUQ_OK;
     }
+    // below a rank-deficient node, a node whose four blocks are base cases
+    // runs as one step on the device (launch_node): one launch, one round trip
+    if (eager && g_tune_node.load(std::memory_order_relaxed) && m <= 2 * c.leaf &&
+        n <= 2 * c.leaf) {
+        const int32_t seq = ++c.hw->seq;
+        PLUQ_TRY(launch_node(A, m, n, lda, c.F, pp, pq, c.d_rank + 4, c.st, c.hw->d, seq, false,
+                             c.gather, c.icopy));
+        PLUQ_TRY(wait_words(c.hw, seq, c.st));
+        const int32_t r = c.hw->h[1];
+        ++c.leaves;
+        if (r < 0 && leaf_error_flag()) return PLUQ_ETIMEOUT;
+        if (r < 0 || r > m || r > n) return PLUQ_EINTERNAL;
+        out.r = r;
+        out.pid = c.hw->h[2] != 0;
+        out.qid = c.hw->h[3] != 0;
+        return PLUQ_OK;
+    }
     // A block's rank is the number of ones of R inside it, so deep in the
     // recursion of a rank-deficient matrix most blocks are exactly zero: one
     // pass over the block prunes the whole subtree (r = 0, P = Q = I).  Below a
@@ -828,6 +846,15 @@ pluq_status pluq_set_leaf_variant(int left_looking)
 }
 
 int pluq_get_leaf_variant(void) { return g_tune_leaf_left.load() ? 1 : 0; }
+
+pluq_status pluq_set_node_kernel(int on)
+{
+    if (on != 0 && on != 1) return PLUQ_EINVAL;
+    g_tune_node.store(on != 0);
+    return PLUQ_OK;
+}
+
+int pluq_get_node_kernel(void) { return g_tune_node.load() ? 1 : 0; }
 
 pluq_status pluq_set_wait_limit(int64_t tries)
 {

@@ -594,16 +594,14 @@ __device__ bool generic_lu(uint32_t *__restrict__ A, int m, int n, int64_t lda, 
 
 // CPL column slots per lane (block width <= 32 CPL), RPW row slots per warp
 // (block height <= NW RPW): only slots that can hold data are compiled in.
+// The base case on the block at A with the thread block's shared memory S:
+// the body of leaf_kernel, also run by the node kernel for its four blocks.
 template <bool SMALLP, int CPL, int RPW>
-__global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int m, int n,
-                                                  int64_t lda, Field F, int32_t *perm_p_out,
-                                                  int32_t *perm_q_out, int32_t *info_out,
-                                                  int info_len, volatile int32_t *host_info,
-                                                  int32_t seq, int try_generic, uint32_t wait_limit,
-                                                  int left_looking)
+__device__ void leaf_run(LeafShared &S, uint32_t *__restrict__ A, int m, int n, int64_t lda,
+                         Field F, int32_t *perm_p_out, int32_t *perm_q_out, int32_t *info_out,
+                         int info_len, volatile int32_t *host_info, int32_t seq, int try_generic,
+                         uint32_t wait_limit, int left_looking)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t p = F.p;
     const Field32 F32{p, 0xFFFFFFFFu / p};
@@ -720,7 +718,12 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
         }
         ++r;
     }
-    if (__syncthreads_or(failed)) {
+    // every warp is past its last step wait: the step barrier is retired, so
+    // that a later base case in the same thread block (the node kernel) may
+    // initialise it afresh
+    const bool any_failed = __syncthreads_or(failed);
+    if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+    if (any_failed) {
         if (tid == 0) {
             info_out[0] = -1;
             if (host_info) {
@@ -901,7 +904,354 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
     }
 }
 
+template <bool SMALLP, int CPL, int RPW>
+__global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int m, int n,
+                                                  int64_t lda, Field F, int32_t *perm_p_out,
+                                                  int32_t *perm_q_out, int32_t *info_out,
+                                                  int info_len, volatile int32_t *host_info,
+                                                  int32_t seq, int try_generic, uint32_t wait_limit,
+                                                  int left_looking)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
+    leaf_run<SMALLP, CPL, RPW>(S, A, m, n, lda, F, perm_p_out, perm_q_out, info_out, info_len,
+                               host_info, seq, try_generic, wait_limit, left_looking);
+}
+
+// ------------------------------------------------------------ node kernel --
+// One step of Algorithm 1 on a node whose four blocks A1, F, G, R are base
+// cases (both sides at most twice the leaf size), run by one thread block:
+// the leaves through leaf_run, the permutations, triangular solves and
+// products between them by the whole block on data that stays in L2.  It
+// replaces a dozen launches and four host round trips by one of each, which
+// pays where the blocks have few pivots (deep in a rank-deficient matrix);
+// the host uses it only below rank-deficient nodes.  Every helper ends with a
+// block-wide barrier, so each step sees the previous one complete.
+
+// X (rows x cols, stride ld) <- X[rmap[i]][cmap[j]] (a null map is the
+// identity), through the global staging area `stage`
+__device__ void nd_perm(uint32_t *X, int64_t ld, int rows, int cols, const int32_t *rmap,
+                        const int32_t *cmap, uint32_t *stage)
+{
+    if (rows <= 0 || cols <= 0 || (!rmap && !cmap)) return;
+    const int tot = rows * cols;
+    for (int e = threadIdx.x; e < tot; e += LT) {
+        const int i = e / cols, j = e - (e / cols) * cols;
+        stage[e] = X[(int64_t)(rmap ? rmap[i] : i) * ld + (cmap ? cmap[j] : j)];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tot; e += LT) {
+        const int i = e / cols, j = e - (e / cols) * cols;
+        X[(int64_t)i * ld + j] = stage[e];
+    }
+    __syncthreads();
+}
+
+// dst (rows x cols) <- src
+__device__ void nd_copy(uint32_t *dst, int64_t ldd, const uint32_t *src, int64_t lds, int rows,
+                        int cols)
+{
+    const int tot = rows * cols;
+    for (int e = threadIdx.x; e < tot; e += LT) {
+        const int i = e / cols, j = e - (e / cols) * cols;
+        dst[(int64_t)i * ldd + j] = src[(int64_t)i * lds + j];
+    }
+    __syncthreads();
+}
+
+// B (r x N) <- L^{-1} B, L unit lower (diagonal not read): a thread per column,
+// each unknown one delayed-reduction dot product over the earlier ones
+template <bool SMALLP>
+__device__ void nd_trsm_left(const uint32_t *L, int64_t ldl, uint32_t *B, int64_t ldb, int r, int N,
+                             const Field &F)
+{
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    if (r > 1)
+        for (int j = threadIdx.x; j < N; j += LT)
+            for (int i = 1; i < r; ++i) {
+                LAcc<SMALLP> acc;
+                for (int l = 0; l < i; ++l) acc.add(L[(int64_t)i * ldl + l], B[(int64_t)l * ldb + j]);
+                B[(int64_t)i * ldb + j] = sub_mod(B[(int64_t)i * ldb + j], acc.value(F, w16), F.p);
+            }
+    __syncthreads();
+}
+
+// B (M x r) <- B U^{-1}, U upper with nonzero diagonal: a thread per row;
+// dinv (r words of shared memory) receives the inverses of the diagonal
+template <bool SMALLP>
+__device__ void nd_trsm_right(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb, int M, int r,
+                              const Field &F, uint32_t *dinv)
+{
+    if (r <= 0 || M <= 0) return;
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    for (int t = threadIdx.x; t < r; t += LT) dinv[t] = inv_mod(U[(int64_t)t * ldu + t], F.p);
+    __syncthreads();
+    for (int i = threadIdx.x; i < M; i += LT) {
+        uint32_t *row = B + (int64_t)i * ldb;
+        for (int j = 0; j < r; ++j) {
+            LAcc<SMALLP> acc;
+            for (int l = 0; l < j; ++l) acc.add(U[(int64_t)l * ldu + j], row[l]);
+            row[j] = mul_mod(sub_mod(row[j], acc.value(F, w16), F.p), dinv[j], F);
+        }
+    }
+    __syncthreads();
+}
+
+// C (M x N) <- C - A B, A M x K, B K x N: each output one delayed reduction
+template <bool SMALLP>
+__device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                          const uint32_t *B, int64_t ldb, int M, int N, int K, const Field &F)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return;
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    const int tot = M * N;
+    for (int e = threadIdx.x; e < tot; e += LT) {
+        const int i = e / N, j = e - (e / N) * N;
+        LAcc<SMALLP> acc;
+        for (int l = 0; l < K; ++l) acc.add(A[(int64_t)i * lda + l], B[(int64_t)l * ldb + j]);
+        C[(int64_t)i * ldc + j] = sub_mod(C[(int64_t)i * ldc + j], acc.value(F, w16), F.p);
+    }
+    __syncthreads();
+}
+
+constexpr int NMAX = 2 * LM;   // largest node side
+
+struct NodeShared {
+    int32_t pv[8][LM];         // P1, Q1, P2, Q2, P3, Q3, P4, Q4 of the four blocks
+    int32_t smap[NMAX], tmap[NMAX];
+    int32_t info[4][3];        // r, P identity, Q identity of each block
+    uint32_t dinv[LM];
+    int nz, sid, tid_ok;
+};
+
+struct NodeArgs {
+    uint32_t *A;
+    int m, n;
+    int64_t lda;
+    Field F;
+    int32_t *perm_p, *perm_q;  // m, n
+    int32_t *info;             // r, P identity, Q identity
+    volatile int32_t *host_info;
+    int32_t seq;
+    uint32_t *stage;           // at least m * n words
+    uint32_t *icopy;           // at least LM * LM words
+    uint32_t wait_limit;
+    int try_generic, left_looking;
+};
+
+// the base case for blocks of up to LM x LM, compiled once for the node
+// kernel's four calls
+template <bool SMALLP>
+__device__ __noinline__ void leaf_run_full(LeafShared &S, uint32_t *A, int m, int n, int64_t lda,
+                                           Field F, int32_t *pp, int32_t *pq, int32_t *info,
+                                           int try_generic, uint32_t wait_limit, int left_looking)
+{
+    leaf_run<SMALLP, 4, 8>(S, A, m, n, lda, F, pp, pq, info, 3, nullptr, 0, try_generic,
+                           wait_limit, left_looking);
+}
+
+// the leaf on block c (0 A1, 1 F, 2 G, 3 R); an empty block has r = 0 and
+// identity permutations
+template <bool SMALLP>
+__device__ void nd_leaf(LeafShared &S, NodeShared &N, int c, uint32_t *X, int mb, int nb,
+                        const NodeArgs &a, int try_generic)
+{
+    if (mb <= 0 || nb <= 0) {
+        if (threadIdx.x == 0) {
+            N.info[c][0] = 0;
+            N.info[c][1] = 1;
+            N.info[c][2] = 1;
+        }
+        __syncthreads();
+        return;
+    }
+    leaf_run_full<SMALLP>(S, X, mb, nb, a.lda, a.F, N.pv[2 * c], N.pv[2 * c + 1], N.info[c],
+                          try_generic, a.wait_limit, a.left_looking);
+    __syncthreads();
+}
+
+template <bool SMALLP>
+__global__ void __launch_bounds__(LT) node_kernel(const __grid_constant__ NodeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
+    __shared__ NodeShared N;
+    const int tid = threadIdx.x;
+    const int m = a.m, n = a.n, k = m / 2, h = n / 2;
+    const int64_t lda = a.lda;
+    const Field F = a.F;
+    uint32_t *A = a.A;
+    auto at = [&](int i, int j) { return A + (int64_t)i * lda + j; };
+    auto publish = [&](int r, int pid, int qid) {
+        if (tid == 0) {
+            a.info[0] = r;
+            a.info[1] = pid;
+            a.info[2] = qid;
+            if (a.host_info) {
+                a.host_info[1] = r;
+                a.host_info[2] = pid;
+                a.host_info[3] = qid;
+                __threadfence_system();
+                a.host_info[0] = a.seq;
+            }
+        }
+    };
+
+    // a zero node is finished: r = 0, P = Q = I
+    bool nz = false;
+    for (int e = tid; e < m * n && !nz; e += LT) nz = *at(e / n, e % n) != 0;
+    if (!__syncthreads_or(nz)) {
+        for (int i = tid; i < m; i += LT) a.perm_p[i] = i;
+        for (int j = tid; j < n; j += LT) a.perm_q[j] = j;
+        publish(0, 1, 1);
+        return;
+    }
+    // A1 = P1 [L1; M1] [U1 V1] Q1
+    nd_leaf<SMALLP>(S, N, 0, A, k, h, a, a.try_generic);
+    const int r1 = N.info[0][0];
+    if (r1 < 0) {
+        publish(-1, 0, 0);
+        return;
+    }
+    const int32_t *P1 = N.info[0][1] ? nullptr : N.pv[0];
+    const int32_t *Q1 = N.info[0][2] ? nullptr : N.pv[1];
+    const int deficient = r1 < (k < h ? k : h);
+    const int tg = deficient ? 0 : 1;
+    // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
+    nd_perm(at(0, h), lda, k, n - h, P1, nullptr, a.stage);
+    nd_perm(at(k, 0), lda, m - k, h, nullptr, Q1, a.stage);
+    // D <- L1^{-1} B1 ; E <- C1 U1^{-1} ; [F;H] <- [B2;A4] - [M1;E] D ; G <- C2 - E V1
+    nd_trsm_left<SMALLP>(A, lda, at(0, h), lda, r1, n - h, F);
+    nd_trsm_right<SMALLP>(A, lda, at(k, 0), lda, m - k, r1, F, N.dinv);
+    nd_mm_sub<SMALLP>(at(r1, h), lda, at(r1, 0), lda, at(0, h), lda, m - r1, n - h, r1, F);
+    nd_mm_sub<SMALLP>(at(k, r1), lda, at(k, 0), lda, at(0, r1), lda, m - k, h - r1, r1, F);
+    // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
+    nd_leaf<SMALLP>(S, N, 1, at(r1, h), k - r1, n - h, a, tg);
+    nd_leaf<SMALLP>(S, N, 2, at(k, r1), m - k, h - r1, a, tg);
+    const int r2 = N.info[1][0], r3 = N.info[2][0];
+    if (r2 < 0 || r3 < 0) {
+        publish(-1, 0, 0);
+        return;
+    }
+    const int32_t *P2 = N.info[1][1] ? nullptr : N.pv[2];
+    const int32_t *Q2 = N.info[1][2] ? nullptr : N.pv[3];
+    const int32_t *P3 = N.info[2][1] ? nullptr : N.pv[4];
+    const int32_t *Q3 = N.info[2][2] ? nullptr : N.pv[5];
+    // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
+    nd_perm(at(k, h), lda, m - k, n - h, P3, Q2, a.stage);
+    nd_perm(at(k, 0), lda, m - k, r1, P3, nullptr, a.stage);
+    nd_perm(at(r1, 0), lda, k - r1, r1, P2, nullptr, a.stage);
+    nd_perm(at(0, h), lda, r1, n - h, nullptr, Q2, a.stage);
+    nd_perm(at(0, r1), lda, r1, h - r1, nullptr, Q3, a.stage);
+    // [I;K] <- [H1;H3] U2^{-1} ; keep I ; [J N] <- L3^{-1} [I H2]
+    nd_trsm_right<SMALLP>(at(r1, h), lda, at(k, h), lda, m - k, r2, F, N.dinv);
+    if (r3 > 0 && r2 > 0) nd_copy(a.icopy, r2, at(k, h), lda, r3, r2);
+    nd_trsm_left<SMALLP>(at(k, r1), lda, at(k, h), lda, r3, n - h, F);
+    // O <- N - J V2 ; R <- H4 - K V2 ; I back ; R <- R - M3 O
+    nd_mm_sub<SMALLP>(at(k, h + r2), lda, at(k, h), lda, at(r1, h + r2), lda, r3, n - h - r2, r2, F);
+    nd_mm_sub<SMALLP>(at(k + r3, h + r2), lda, at(k + r3, h), lda, at(r1, h + r2), lda, m - k - r3,
+                      n - h - r2, r2, F);
+    if (r3 > 0 && r2 > 0) nd_copy(at(k, h), lda, a.icopy, r2, r3, r2);
+    nd_mm_sub<SMALLP>(at(k + r3, h + r2), lda, at(k + r3, r1), lda, at(k, h + r2), lda, m - k - r3,
+                      n - h - r2, r3, F);
+    // R = P4 [L4;M4][U4 V4] Q4
+    nd_leaf<SMALLP>(S, N, 3, at(k + r3, h + r2), m - k - r3, n - h - r2, a, tg);
+    const int r4 = N.info[3][0];
+    if (r4 < 0) {
+        publish(-1, 0, 0);
+        return;
+    }
+    const int32_t *P4 = N.info[3][1] ? nullptr : N.pv[6];
+    const int32_t *Q4 = N.info[3][2] ? nullptr : N.pv[7];
+    // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T
+    nd_perm(at(k + r3, 0), lda, m - k - r3, h + r2, P4, nullptr, a.stage);
+    nd_perm(at(0, h + r2), lda, k + r3, n - h - r2, nullptr, Q4, a.stage);
+    // P = Diag(P1 diag(I,P2), P3 diag(I,P4)) S, Q = T Diag(diag(I,Q3) Q1, diag(I,Q4) Q2),
+    // and the row map of S / column map of T
+    auto ap = [](const int32_t *v, int x) { return v ? v[x] : x; };
+    bool s_same = true, t_same = true;
+    for (int i = tid; i < m; i += LT) {
+        const int top = r1 + r2, bot = r3 + r4;
+        const int sr = i < top ? i : (i < top + bot ? k + (i - top) : (i < k + bot ? i - bot : i));
+        N.smap[i] = sr;
+        s_same &= sr == i;
+        int d;
+        if (sr < k) d = sr < r1 ? ap(P1, sr) : ap(P1, r1 + ap(P2, sr - r1));
+        else {
+            const int u = sr - k;
+            d = k + (u < r3 ? ap(P3, u) : ap(P3, r3 + ap(P4, u - r3)));
+        }
+        a.perm_p[i] = d;
+    }
+    for (int j = tid; j < n; j += LT) {
+        int c;
+        if (j < r1) c = j;
+        else if (j < r1 + r2) c = h + (j - r1);
+        else if (j < r1 + r2 + r3) c = r1 + (j - r1 - r2);
+        else if (j < r1 + r2 + r3 + r4) c = h + r2 + (j - r1 - r2 - r3);
+        else if (j < h + r2 + r4) c = r1 + r3 + (j - r1 - r2 - r3 - r4);
+        else c = j;
+        N.tmap[j] = c;
+        t_same &= c == j;
+        int d;
+        if (c < h) d = c < r1 ? ap(Q1, c) : ap(Q1, r1 + ap(Q3, c - r1));
+        else {
+            const int u = c - h;
+            d = h + (u < r2 ? ap(Q2, u) : ap(Q2, r2 + ap(Q4, u - r2)));
+        }
+        a.perm_q[j] = d;
+    }
+    const bool s_ident = __syncthreads_and(s_same);
+    const bool t_ident = __syncthreads_and(t_same);
+    // A <- S^T A T^T
+    nd_perm(A, lda, m, n, s_ident ? nullptr : N.smap, t_ident ? nullptr : N.tmap, a.stage);
+    int pid = s_ident, qid = t_ident;
+    for (int c = 0; c < 4; ++c) {
+        pid &= N.info[c][1] != 0;
+        qid &= N.info[c][2] != 0;
+    }
+    publish(r1 + r2 + r3 + r4, pid, qid);
+}
+
 }  // namespace
+
+pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F, int32_t *perm_p,
+                        int32_t *perm_q, int32_t *info, cudaStream_t st, volatile int32_t *host_info,
+                        int32_t seq, bool try_generic, uint32_t *stage, uint32_t *icopy)
+{
+    if (m <= 0 || n <= 0 || m > NMAX || n > NMAX) return PLUQ_EINVAL;
+    NodeArgs a{};
+    a.A = A;
+    a.m = (int)m;
+    a.n = (int)n;
+    a.lda = lda;
+    a.F = F;
+    a.perm_p = perm_p;
+    a.perm_q = perm_q;
+    a.info = info;
+    a.host_info = host_info;
+    a.seq = seq;
+    a.stage = stage;
+    a.icopy = icopy;
+    a.wait_limit = wait_limit_or(STEP_WAIT_LIMIT);
+    a.try_generic = try_generic ? 1 : 0;
+    a.left_looking = g_tune_leaf_left.load(std::memory_order_relaxed) ? 1 : 0;
+    const size_t smem = sizeof(LeafShared);
+    prof::start(prof::LEAF, st);
+    if (F.p <= 65536u) {
+        static std::atomic<uint64_t> attr{0};
+        if (!smem_attr_once((const void *)node_kernel<true>, smem, attr)) return PLUQ_ECUDA;
+        node_kernel<true><<<1, LT, smem, st>>>(a);
+    } else {
+        static std::atomic<uint64_t> attr{0};
+        if (!smem_attr_once((const void *)node_kernel<false>, smem, attr)) return PLUQ_ECUDA;
+        node_kernel<false><<<1, LT, smem, st>>>(a);
+    }
+    pluq_status s = last_launch();
+    const double kk = (double)(m < n ? m : n);
+    prof::stop(prof::LEAF, st, 2.0 * m * n * kk - (double)(m + n) * kk * kk + 2.0 / 3.0 * kk * kk * kk);
+    return s;
+}
 
 pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F, int32_t *perm_p,
                         int32_t *perm_q, int32_t *info, int info_len, cudaStream_t st,

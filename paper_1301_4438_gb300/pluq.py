@@ -90,6 +90,8 @@ _SIGS = {
     "pluq_set_wait_limit": (ctypes.c_int, [_c_i64]),
     "pluq_set_leaf_variant": (ctypes.c_int, [ctypes.c_int]),
     "pluq_get_leaf_variant": (ctypes.c_int, []),
+    "pluq_set_node_kernel": (ctypes.c_int, [ctypes.c_int]),
+    "pluq_get_node_kernel": (ctypes.c_int, []),
     "pluq_device_status": (ctypes.c_int, [_vp]),
     "pluq_get_lazy_zero_test": (ctypes.c_int, []),
     "pluq_launch_count": (ctypes.c_longlong, []),
@@ -614,3 +616,12 @@ def pluq_cup(LU: torch.Tensor, perm_p: torch.Tensor, perm_q: torch.Tensor, r: in
     with A[:, perm] = C U, C in column echelon form, U unit upper trapezoidal."""
     m, n = LU.shape
     return _echelon(load().pluq_cup, LU, perm_p, perm_q, r, p, mm, stream, n, (m, r), (r, n))
+
+
+def pluq_set_node_kernel(on: bool):
+    """Small nodes below rank-deficient ones as one device step (speed only)."""
+    _check(load().pluq_set_node_kernel(1 if on else 0), "pluq_set_node_kernel")
+
+
+def pluq_get_node_kernel() -> bool:
+    return bool(load().pluq_get_node_kernel())

@@ -128,3 +128,34 @@ def test_tuning_knobs_do_not_change_results():
         assert all(np.array_equal(x, y) for x, y in zip(o[:3], outs[0][:3]))
     LU0, pp0, pq0, r0 = oracle.pluq(A, p)
     assert np.array_equal(outs[0][0], LU0)
+
+
+@pytest.mark.parametrize("node", [True, False])
+@pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
+def test_node_kernel_matches_oracle(p, node):
+    """With the node kernel on, nodes of at most twice the leaf size below
+    rank-deficient nodes are computed in one thread block; with it off they
+    take the host-driven path.  Either way results stay element-wise equal to
+    the oracle (planted profiles of several densities,
+    a clustered profile, sparse and low-rank products, rectangular shapes)."""
+    g = np.random.Generator(np.random.PCG64(p + 99))
+    old = pluq.pluq_get_node_kernel()
+    pluq.pluq_set_node_kernel(node)
+    try:
+        cases = [W.planted(256, 256, 60, p, 1)[0], W.planted(300, 200, 150, p, 2)[0],
+                 W.planted(700, 500, 120, p, 3)[0], W.planted(520, 900, 400, p, 4)[0],
+                 W.planted(400, 400, 200, p, 5, pivot_rows=W.clustered_rows(400, 200, 100, 6))[0],
+                 (g.integers(0, p, (600, 450)) * (g.random((600, 450)) < 0.01)).astype(np.uint32)]
+        X = g.integers(0, p, (640, 40)).astype(np.int64)
+        Y = g.integers(0, p, (40, 610)).astype(np.int64)
+        cases.append((X.astype(object).dot(Y.astype(object)) % p).astype(np.uint32))
+        for A in cases:
+            LU0, pp0, pq0, r0 = oracle.pluq(A, p)
+            d = torch.from_numpy(A.astype(np.int32)).cuda()
+            pp, pq, r = pluq.pluq_mod_p(d, p)
+            assert r == r0, A.shape
+            assert np.array_equal(pp.cpu().numpy(), pp0), A.shape
+            assert np.array_equal(pq.cpu().numpy(), pq0), A.shape
+            assert np.array_equal(d.cpu().numpy().astype(np.uint32), LU0), A.shape
+    finally:
+        pluq.pluq_set_node_kernel(old)
