@@ -308,7 +308,7 @@ def tune_for(cfg, m, n, p):
     pluq.pluq_set_branch_min(tuned[2])
     pluq.pluq_set_lazy_zero_test(bool(tuned[3]))
     pluq.pluq_set_leaf_variant(bool(tuned[4]))
-    pluq.pluq_set_node_kernel(bool(tuned[5]))
+    pluq.pluq_set_node_kernel(int(tuned[5]))
     return tuned
 
 
@@ -712,7 +712,7 @@ def run_ours(args):
                                             "small-product threshold {2^24,2^25,2^27}, "
                                             "branch threshold {32,64,128,off}, zero test "
                                             "{awaited,lazy}, base case {right,left}-looking, "
-                                            "node kernel {on,off}"}},
+                                            "node kernel levels {1,2,0}"}},
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,

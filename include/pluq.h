@@ -441,15 +441,15 @@ int pluq_get_leaf_variant(void);
 
 /*
  * Node kernel (speed only, never results): below a rank-deficient node of
- * the recursion, a node whose four blocks A1, F, G, R are all base cases
- * (both sides at most twice the leaf size) is computed by one thread block in
- * one launch -- the four base cases and the permutations, triangular solves
- * and products of Algorithm 1's step between them -- instead of a dozen
- * launches and four host round trips.  It pays where those blocks hold few
- * pivots, deep in a rank-deficient matrix.  1 enables it (the default), 0
- * keeps every node on the host-driven path.  EINVAL unless 0 or 1.
+ * the recursion, a node of at most 2 x leaf (levels >= 1) or 4 x leaf
+ * (levels = 2) on a side is computed by one thread block in one launch -- its
+ * base cases and the permutations, triangular solves and products of
+ * Algorithm 1's steps between them (for 4 x leaf, two levels of steps) --
+ * instead of dozens of launches and host round trips.  It pays where those
+ * blocks hold few pivots, deep in a rank-deficient matrix.  levels = 0 keeps
+ * every node on the host-driven path.  Default 1; EINVAL outside 0..2.
  */
-pluq_status pluq_set_node_kernel(int on);
+pluq_status pluq_set_node_kernel(int levels);
 int pluq_get_node_kernel(void);
 
 /*

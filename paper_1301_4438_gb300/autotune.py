@@ -30,7 +30,7 @@ SMALL_MM = (1 << 24, 1 << 25, 1 << 27)
 BRANCH = (32, 64, 128, 1 << 40)          # 2^40: never hand G to another thread
 LAZY_ZERO = (0, 1)
 LEAF_LEFT = (0, 1)                       # base case right- / left-looking
-NODE = (1, 0)                            # small deficient nodes in one thread block
+NODE = (1, 2, 0)                         # device-side levels of small deficient nodes
 DEFAULT = (128, 1 << 25, 64, 0, 0, 1)
 KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT, NODE)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pluq_gb300", "tuning.json")
@@ -91,7 +91,7 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
         pluq.pluq_set_branch_min(cand[2])
         pluq.pluq_set_lazy_zero_test(bool(cand[3]))
         pluq.pluq_set_leaf_variant(bool(cand[4]))
-        pluq.pluq_set_node_kernel(bool(cand[5]))
+        pluq.pluq_set_node_kernel(int(cand[5]))
         times = []
         for _ in range(reps + 1):
             A = A0.clone()
@@ -141,5 +141,5 @@ def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_
     if "leaf_left" in ent:
         pluq.pluq_set_leaf_variant(bool(ent["leaf_left"]))
     if "node" in ent:
-        pluq.pluq_set_node_kernel(bool(ent["node"]))
+        pluq.pluq_set_node_kernel(int(ent["node"]))
     return True

@@ -352,9 +352,10 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
                         cudaStream_t st, volatile int32_t *host_info = nullptr, int32_t seq = 0,
                         bool try_generic = true);
 
-// One step of Algorithm 1 on a node of at most 2 LEAF_MAX x 2 LEAF_MAX whose
-// four blocks are base cases, in one thread block (same outputs and host
-// words as launch_leaf); stage holds m * n words, icopy LEAF_MAX^2.
+// Algorithm 1 on a node of at most 4 LEAF_MAX x 4 LEAF_MAX in one thread
+// block: its blocks are base cases, or (above 2 LEAF_MAX) nodes whose blocks
+// are; same outputs and host words as launch_leaf.  stage holds m * n words,
+// icopy ceil(m/2) * ceil(n/2).
 pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F, int32_t *perm_p,
                         int32_t *perm_q, int32_t *info, cudaStream_t st, volatile int32_t *host_info,
                         int32_t seq, bool try_generic, uint32_t *stage, uint32_t *icopy);
@@ -366,8 +367,8 @@ extern std::atomic<int64_t> g_tune_leaf;
 extern std::atomic<int64_t> g_tune_small_mm;
 // base case: right-looking (false) or left-looking (true) blocked elimination
 extern std::atomic<bool> g_tune_leaf_left;
-// nodes below rank-deficient ones whose four blocks are base cases go to the
-// node kernel when true
-extern std::atomic<bool> g_tune_node;
+// nodes below rank-deficient ones of at most 2 levels x 2 x leaf on a side go
+// to the node kernel (0: none)
+extern std::atomic<int> g_tune_node;
 
 }  // namespace pluq

@@ -43,7 +43,7 @@ std::atomic<int64_t> g_tune_leaf{128};
 std::atomic<int64_t> g_tune_branch{64};
 std::atomic<int64_t> g_wait_limit{-1};
 std::atomic<bool> g_tune_leaf_left{false};
-std::atomic<bool> g_tune_node{true};
+std::atomic<int> g_tune_node{1};
 // zero test of a block below a rank-deficient node: false = wait for it before
 // descending (a zero block costs one round trip), true = read it with the first
 // leaf of the descent (a nonzero block costs nothing extra)
@@ -499,8 +499,9 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     }
     // below a rank-deficient node, a node whose four blocks are base cases
     // runs as one step on the device (launch_node): one launch, one round trip
-    if (eager && g_tune_node.load(std::memory_order_relaxed) && m <= 2 * c.leaf &&
-        n <= 2 * c.leaf) {
+    const int node_levels = g_tune_node.load(std::memory_order_relaxed);
+    const int64_t node_side = std::min<int64_t>((int64_t)2 * node_levels * c.leaf, 4 * LEAF_MAX);
+    if (eager && node_levels > 0 && m <= node_side && n <= node_side) {
         const int32_t seq = ++c.hw->seq;
         PLUQ_TRY(launch_node(A, m, n, lda, c.F, pp, pq, c.d_rank + 4, c.st, c.hw->d, seq, false,
                              c.gather, c.icopy));
@@ -847,14 +848,14 @@ pluq_status pluq_set_leaf_variant(int left_looking)
 
 int pluq_get_leaf_variant(void) { return g_tune_leaf_left.load() ? 1 : 0; }
 
-pluq_status pluq_set_node_kernel(int on)
+pluq_status pluq_set_node_kernel(int levels)
 {
-    if (on != 0 && on != 1) return PLUQ_EINVAL;
-    g_tune_node.store(on != 0);
+    if (levels < 0 || levels > 2) return PLUQ_EINVAL;
+    g_tune_node.store(levels);
     return PLUQ_OK;
 }
 
-int pluq_get_node_kernel(void) { return g_tune_node.load() ? 1 : 0; }
+int pluq_get_node_kernel(void) { return g_tune_node.load(); }
 
 pluq_status pluq_set_wait_limit(int64_t tries)
 {

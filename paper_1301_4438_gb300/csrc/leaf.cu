@@ -1014,14 +1014,22 @@ __device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t l
     __syncthreads();
 }
 
-constexpr int NMAX = 2 * LM;   // largest node side
+constexpr int NMAX = 4 * LM;   // largest node side (two levels above the leaves)
+
+// Per-level state of a node step: the permutations of its four blocks, the
+// maps of S and T, and each block's r / P identity / Q identity.  A step of
+// level l has blocks of sides up to (l == 1 ? LM : 2 LM).
+template <int V>
+struct NodeLevel {
+    int32_t pv[8][V];          // P1, Q1, P2, Q2, P3, Q3, P4, Q4
+    int32_t smap[2 * V], tmap[2 * V];
+    int32_t info[4][3];
+};
 
 struct NodeShared {
-    int32_t pv[8][LM];         // P1, Q1, P2, Q2, P3, Q3, P4, Q4 of the four blocks
-    int32_t smap[NMAX], tmap[NMAX];
-    int32_t info[4][3];        // r, P identity, Q identity of each block
-    uint32_t dinv[LM];
-    int nz, sid, tid_ok;
+    NodeLevel<LM> l1;
+    NodeLevel<2 * LM> l2;
+    uint32_t dinv[2 * LM];
 };
 
 struct NodeArgs {
@@ -1034,13 +1042,13 @@ struct NodeArgs {
     volatile int32_t *host_info;
     int32_t seq;
     uint32_t *stage;           // at least m * n words
-    uint32_t *icopy;           // at least LM * LM words
+    uint32_t *icopy;           // at least (m/2 + 1) * (n/2 + 1) words
     uint32_t wait_limit;
     int try_generic, left_looking;
 };
 
 // the base case for blocks of up to LM x LM, compiled once for the node
-// kernel's four calls
+// steps' calls
 template <bool SMALLP>
 __device__ __noinline__ void leaf_run_full(LeafShared &S, uint32_t *A, int m, int n, int64_t lda,
                                            Field F, int32_t *pp, int32_t *pq, int32_t *info,
@@ -1050,87 +1058,89 @@ __device__ __noinline__ void leaf_run_full(LeafShared &S, uint32_t *A, int m, in
                            wait_limit, left_looking);
 }
 
-// the leaf on block c (0 A1, 1 F, 2 G, 3 R); an empty block has r = 0 and
-// identity permutations
-template <bool SMALLP>
-__device__ void nd_leaf(LeafShared &S, NodeShared &N, int c, uint32_t *X, int mb, int nb,
-                        const NodeArgs &a, int try_generic)
+template <int LEVEL>
+__device__ __forceinline__ auto &node_level(NodeShared &N)
 {
-    if (mb <= 0 || nb <= 0) {
-        if (threadIdx.x == 0) {
-            N.info[c][0] = 0;
-            N.info[c][1] = 1;
-            N.info[c][2] = 1;
-        }
-        __syncthreads();
-        return;
-    }
-    leaf_run_full<SMALLP>(S, X, mb, nb, a.lda, a.F, N.pv[2 * c], N.pv[2 * c + 1], N.info[c],
-                          try_generic, a.wait_limit, a.left_looking);
-    __syncthreads();
+    if constexpr (LEVEL == 1) return N.l1;
+    else return N.l2;
 }
 
-template <bool SMALLP>
-__global__ void __launch_bounds__(LT) node_kernel(const __grid_constant__ NodeArgs a)
+// One step of Algorithm 1 on the m x n block at A (both sides at most 2^LEVEL
+// LM) by the whole thread block: blocks that are base cases go to
+// leaf_run_full, larger ones (LEVEL 2) to a step of level 1.  Writes P / Q to
+// pp / pq and r, P identity, Q identity to info[0..2] (-1 for r if a base
+// case gave up a bounded wait).
+template <bool SMALLP, int LEVEL>
+__device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const NodeArgs &a,
+                                       uint32_t *A, int m, int n, int32_t *pp, int32_t *pq,
+                                       int32_t *info, int try_generic)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
-    __shared__ NodeShared N;
+    auto &N = node_level<LEVEL>(NS);
     const int tid = threadIdx.x;
-    const int m = a.m, n = a.n, k = m / 2, h = n / 2;
+    const int k = m / 2, h = n / 2;
     const int64_t lda = a.lda;
     const Field F = a.F;
-    uint32_t *A = a.A;
     auto at = [&](int i, int j) { return A + (int64_t)i * lda + j; };
-    auto publish = [&](int r, int pid, int qid) {
+    auto done = [&](int r, int pid, int qid) {
         if (tid == 0) {
-            a.info[0] = r;
-            a.info[1] = pid;
-            a.info[2] = qid;
-            if (a.host_info) {
-                a.host_info[1] = r;
-                a.host_info[2] = pid;
-                a.host_info[3] = qid;
-                __threadfence_system();
-                a.host_info[0] = a.seq;
-            }
+            info[0] = r;
+            info[1] = pid;
+            info[2] = qid;
         }
+        __syncthreads();
+    };
+    // block c (0 A1, 1 F, 2 G, 3 R); an empty block has r = 0, P = Q = I
+    auto child = [&](int c, uint32_t *X, int mb, int nb, int tg) {
+        if (mb <= 0 || nb <= 0) {
+            if (tid == 0) {
+                N.info[c][0] = 0;
+                N.info[c][1] = 1;
+                N.info[c][2] = 1;
+            }
+        } else if (mb <= LM && nb <= LM) {
+            leaf_run_full<SMALLP>(S, X, mb, nb, lda, F, N.pv[2 * c], N.pv[2 * c + 1], N.info[c],
+                                  tg, a.wait_limit, a.left_looking);
+        } else {
+            if constexpr (LEVEL > 1)
+                node_step<SMALLP, LEVEL - 1>(S, NS, a, X, mb, nb, N.pv[2 * c], N.pv[2 * c + 1],
+                                             N.info[c], tg);
+        }
+        __syncthreads();
     };
 
-    // a zero node is finished: r = 0, P = Q = I
+    // a zero block is finished: r = 0, P = Q = I
     bool nz = false;
     for (int e = tid; e < m * n && !nz; e += LT) nz = *at(e / n, e % n) != 0;
     if (!__syncthreads_or(nz)) {
-        for (int i = tid; i < m; i += LT) a.perm_p[i] = i;
-        for (int j = tid; j < n; j += LT) a.perm_q[j] = j;
-        publish(0, 1, 1);
+        for (int i = tid; i < m; i += LT) pp[i] = i;
+        for (int j = tid; j < n; j += LT) pq[j] = j;
+        done(0, 1, 1);
         return;
     }
     // A1 = P1 [L1; M1] [U1 V1] Q1
-    nd_leaf<SMALLP>(S, N, 0, A, k, h, a, a.try_generic);
+    child(0, A, k, h, try_generic);
     const int r1 = N.info[0][0];
     if (r1 < 0) {
-        publish(-1, 0, 0);
+        done(-1, 0, 0);
         return;
     }
     const int32_t *P1 = N.info[0][1] ? nullptr : N.pv[0];
     const int32_t *Q1 = N.info[0][2] ? nullptr : N.pv[1];
-    const int deficient = r1 < (k < h ? k : h);
-    const int tg = deficient ? 0 : 1;
+    const int tg = r1 < (k < h ? k : h) ? 0 : 1;
     // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
     nd_perm(at(0, h), lda, k, n - h, P1, nullptr, a.stage);
     nd_perm(at(k, 0), lda, m - k, h, nullptr, Q1, a.stage);
     // D <- L1^{-1} B1 ; E <- C1 U1^{-1} ; [F;H] <- [B2;A4] - [M1;E] D ; G <- C2 - E V1
     nd_trsm_left<SMALLP>(A, lda, at(0, h), lda, r1, n - h, F);
-    nd_trsm_right<SMALLP>(A, lda, at(k, 0), lda, m - k, r1, F, N.dinv);
+    nd_trsm_right<SMALLP>(A, lda, at(k, 0), lda, m - k, r1, F, NS.dinv);
     nd_mm_sub<SMALLP>(at(r1, h), lda, at(r1, 0), lda, at(0, h), lda, m - r1, n - h, r1, F);
     nd_mm_sub<SMALLP>(at(k, r1), lda, at(k, 0), lda, at(0, r1), lda, m - k, h - r1, r1, F);
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
-    nd_leaf<SMALLP>(S, N, 1, at(r1, h), k - r1, n - h, a, tg);
-    nd_leaf<SMALLP>(S, N, 2, at(k, r1), m - k, h - r1, a, tg);
+    child(1, at(r1, h), k - r1, n - h, tg);
+    child(2, at(k, r1), m - k, h - r1, tg);
     const int r2 = N.info[1][0], r3 = N.info[2][0];
     if (r2 < 0 || r3 < 0) {
-        publish(-1, 0, 0);
+        done(-1, 0, 0);
         return;
     }
     const int32_t *P2 = N.info[1][1] ? nullptr : N.pv[2];
@@ -1144,7 +1154,7 @@ __global__ void __launch_bounds__(LT) node_kernel(const __grid_constant__ NodeAr
     nd_perm(at(0, h), lda, r1, n - h, nullptr, Q2, a.stage);
     nd_perm(at(0, r1), lda, r1, h - r1, nullptr, Q3, a.stage);
     // [I;K] <- [H1;H3] U2^{-1} ; keep I ; [J N] <- L3^{-1} [I H2]
-    nd_trsm_right<SMALLP>(at(r1, h), lda, at(k, h), lda, m - k, r2, F, N.dinv);
+    nd_trsm_right<SMALLP>(at(r1, h), lda, at(k, h), lda, m - k, r2, F, NS.dinv);
     if (r3 > 0 && r2 > 0) nd_copy(a.icopy, r2, at(k, h), lda, r3, r2);
     nd_trsm_left<SMALLP>(at(k, r1), lda, at(k, h), lda, r3, n - h, F);
     // O <- N - J V2 ; R <- H4 - K V2 ; I back ; R <- R - M3 O
@@ -1155,10 +1165,10 @@ __global__ void __launch_bounds__(LT) node_kernel(const __grid_constant__ NodeAr
     nd_mm_sub<SMALLP>(at(k + r3, h + r2), lda, at(k + r3, r1), lda, at(k, h + r2), lda, m - k - r3,
                       n - h - r2, r3, F);
     // R = P4 [L4;M4][U4 V4] Q4
-    nd_leaf<SMALLP>(S, N, 3, at(k + r3, h + r2), m - k - r3, n - h - r2, a, tg);
+    child(3, at(k + r3, h + r2), m - k - r3, n - h - r2, tg);
     const int r4 = N.info[3][0];
     if (r4 < 0) {
-        publish(-1, 0, 0);
+        done(-1, 0, 0);
         return;
     }
     const int32_t *P4 = N.info[3][1] ? nullptr : N.pv[6];
@@ -1181,7 +1191,7 @@ __global__ void __launch_bounds__(LT) node_kernel(const __grid_constant__ NodeAr
             const int u = sr - k;
             d = k + (u < r3 ? ap(P3, u) : ap(P3, r3 + ap(P4, u - r3)));
         }
-        a.perm_p[i] = d;
+        pp[i] = d;
     }
     for (int j = tid; j < n; j += LT) {
         int c;
@@ -1199,7 +1209,7 @@ __global__ void __launch_bounds__(LT) node_kernel(const __grid_constant__ NodeAr
             const int u = c - h;
             d = h + (u < r2 ? ap(Q2, u) : ap(Q2, r2 + ap(Q4, u - r2)));
         }
-        a.perm_q[j] = d;
+        pq[j] = d;
     }
     const bool s_ident = __syncthreads_and(s_same);
     const bool t_ident = __syncthreads_and(t_same);
@@ -1210,7 +1220,23 @@ __global__ void __launch_bounds__(LT) node_kernel(const __grid_constant__ NodeAr
         pid &= N.info[c][1] != 0;
         qid &= N.info[c][2] != 0;
     }
-    publish(r1 + r2 + r3 + r4, pid, qid);
+    done(r1 + r2 + r3 + r4, pid, qid);
+}
+
+template <bool SMALLP, int LEVEL>
+__global__ void __launch_bounds__(LT, 1) node_kernel(const __grid_constant__ NodeArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
+    __shared__ NodeShared NS;
+    node_step<SMALLP, LEVEL>(S, NS, a, a.A, a.m, a.n, a.perm_p, a.perm_q, a.info, a.try_generic);
+    if (threadIdx.x == 0 && a.host_info) {
+        a.host_info[1] = a.info[0];
+        a.host_info[2] = a.info[1];
+        a.host_info[3] = a.info[2];
+        __threadfence_system();
+        a.host_info[0] = a.seq;
+    }
 }
 
 }  // namespace
@@ -1237,16 +1263,20 @@ pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     a.try_generic = try_generic ? 1 : 0;
     a.left_looking = g_tune_leaf_left.load(std::memory_order_relaxed) ? 1 : 0;
     const size_t smem = sizeof(LeafShared);
+    const bool two = m > 2 * LM || n > 2 * LM;   // blocks larger than base cases
     prof::start(prof::LEAF, st);
-    if (F.p <= 65536u) {
-        static std::atomic<uint64_t> attr{0};
-        if (!smem_attr_once((const void *)node_kernel<true>, smem, attr)) return PLUQ_ECUDA;
-        node_kernel<true><<<1, LT, smem, st>>>(a);
-    } else {
-        static std::atomic<uint64_t> attr{0};
-        if (!smem_attr_once((const void *)node_kernel<false>, smem, attr)) return PLUQ_ECUDA;
-        node_kernel<false><<<1, LT, smem, st>>>(a);
+#define PLUQ_NODE_CASE(SP, LV)                                                                   \
+    {                                                                                            \
+        static std::atomic<uint64_t> attr{0};                                                    \
+        if (!smem_attr_once((const void *)node_kernel<SP, LV>, smem, attr)) return PLUQ_ECUDA;    \
+        node_kernel<SP, LV><<<1, LT, smem, st>>>(a);                                             \
     }
+    if (F.p <= 65536u) {
+        if (two) PLUQ_NODE_CASE(true, 2) else PLUQ_NODE_CASE(true, 1)
+    } else {
+        if (two) PLUQ_NODE_CASE(false, 2) else PLUQ_NODE_CASE(false, 1)
+    }
+#undef PLUQ_NODE_CASE
     pluq_status s = last_launch();
     const double kk = (double)(m < n ? m : n);
     prof::stop(prof::LEAF, st, 2.0 * m * n * kk - (double)(m + n) * kk * kk + 2.0 / 3.0 * kk * kk * kk);

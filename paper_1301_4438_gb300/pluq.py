@@ -618,10 +618,11 @@ def pluq_cup(LU: torch.Tensor, perm_p: torch.Tensor, perm_q: torch.Tensor, r: in
     return _echelon(load().pluq_cup, LU, perm_p, perm_q, r, p, mm, stream, n, (m, r), (r, n))
 
 
-def pluq_set_node_kernel(on: bool):
-    """Small nodes below rank-deficient ones as one device step (speed only)."""
-    _check(load().pluq_set_node_kernel(1 if on else 0), "pluq_set_node_kernel")
+def pluq_set_node_kernel(levels: int):
+    """Small nodes below rank-deficient ones in one thread block: 0 off, 1 up to
+    2 x leaf, 2 up to 4 x leaf on a side (speed only)."""
+    _check(load().pluq_set_node_kernel(int(levels)), "pluq_set_node_kernel")
 
 
-def pluq_get_node_kernel() -> bool:
-    return bool(load().pluq_get_node_kernel())
+def pluq_get_node_kernel() -> int:
+    return int(load().pluq_get_node_kernel())

@@ -130,12 +130,12 @@ def test_tuning_knobs_do_not_change_results():
     assert np.array_equal(outs[0][0], LU0)
 
 
-@pytest.mark.parametrize("node", [True, False])
+@pytest.mark.parametrize("node", [2, 1, 0])
 @pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
 def test_node_kernel_matches_oracle(p, node):
-    """With the node kernel on, nodes of at most twice the leaf size below
-    rank-deficient nodes are computed in one thread block; with it off they
-    take the host-driven path.  Either way results stay element-wise equal to
+    """With the node kernel on, nodes of at most twice (levels 1) or four times
+    (levels 2) the leaf size below rank-deficient nodes are computed in one
+    thread block; with it off they take the host-driven path.  Either way results stay element-wise equal to
     the oracle (planted profiles of several densities,
     a clustered profile, sparse and low-rank products, rectangular shapes)."""
     g = np.random.Generator(np.random.PCG64(p + 99))
