@@ -18,9 +18,16 @@ namespace pluq {
 // Barrett reduction of x < 2^64 with mu = floor((2^64 - 1) / p): the quotient
 // estimate q = hi64(x * mu) satisfies floor(x/p) - 1 <= q <= floor(x/p), so
 // x - q p lies in [0, 2p) and one conditional subtraction finishes it.
+//
+// Montgomery form with R = 2^32 (odd p only): x is held as x R mod p, and
+// mont_redc(T) = T R^{-1} mod p, in [0, 2p), for T < p R: with
+// m = T pinv mod R (pinv = -1/p mod R), T + m p is divisible by R and below
+// 2 p R, so one multiply-add and a shift replace Barrett's 64-bit high
+// product.  r2 = R^2 mod p converts into the form.
 struct Field {
     uint32_t p;
     uint64_t mu;
+    uint32_t pinv, r2;
 };
 
 inline Field make_field(uint32_t p)
@@ -28,6 +35,13 @@ inline Field make_field(uint32_t p)
     Field f;
     f.p = p;
     f.mu = ~0ull / p;
+    // Newton's iteration x <- x (2 - p x) doubles the bits of 1/p mod 2^32
+    // that are right; x = p is right to 3 bits for odd p (p^2 = 1 mod 8)
+    uint32_t x = p;
+    for (int i = 0; i < 4; ++i) x *= 2u - p * x;
+    f.pinv = (p & 1u) ? 0u - x : 0u;
+    const uint64_t t = (1ull << 32) % p;
+    f.r2 = (uint32_t)(t * t % p);
     return f;
 }
 
@@ -59,6 +73,22 @@ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t p)
     // a - b wraps above 2^32 - p when a < b; adding p then lands in [1, p)
     const uint32_t d = a - b;
     return min(d, d + p);
+}
+
+__device__ __forceinline__ uint32_t mont_redc(uint64_t T, const Field &F)
+{
+    const uint32_t m = (uint32_t)T * F.pinv;
+    return (uint32_t)((T + (uint64_t)m * F.p) >> 32);
+}
+
+__device__ __forceinline__ uint32_t to_mont(uint32_t x, const Field &F)
+{
+    return fold(mont_redc((uint64_t)x * F.r2, F), F.p);
+}
+
+__device__ __forceinline__ uint32_t from_mont(uint32_t x, const Field &F)
+{
+    return fold(mont_redc(x, F), F.p);
 }
 
 // (a*b - c*d) mod p with one reduction: a*b + c*(p-d) < 2^63.

@@ -108,21 +108,28 @@ struct Frame {
 };
 constexpr int MAX_DEPTH = 20;
 
+static_assert(LM == 128, "row and column sets are two 64-bit words");
+
+// the first k (0 <= k <= 128) indices
+__device__ __forceinline__ Mask prefix_mask(int k)
+{
+    return Mask{{k >= 64 ? ~0ull : (1ull << k) - 1ull,
+                 k >= 128 ? ~0ull : (k > 64 ? (1ull << (k - 64)) - 1ull : 0ull)}};
+}
+
+// prow32[w] bit b: row 32 w + b holds a one of R (set by the caller's warps)
 __device__ int order_pivots(Frame *stk, const int32_t *col_of_row, const int32_t *row_of_col,
-                            int m, int n, int32_t *ord_row, int32_t *ord_col)
+                            const uint32_t *prow32, int m, int n, int32_t *ord_row,
+                            int32_t *ord_col)
 {
     int count = 0;
     int top = 0;
-    Mask rows{{0, 0}}, cols{{0, 0}};
-    for (int i = 0; i < m; ++i) set(rows, i);
-    for (int j = 0; j < n; ++j) set(cols, j);
-    stk[0].rows = rows;
-    stk[0].cols = cols;
+    stk[0].rows = prefix_mask(m);
+    stk[0].cols = prefix_mask(n);
     stk[0].stage = 0;
     Mask ret_r{{0, 0}}, ret_c{{0, 0}};   // used masks returned by the last popped frame
-    Mask prow_mask{{0, 0}};               // rows holding a one of R
-    for (int i = 0; i < m; ++i)
-        if (col_of_row[i] >= 0) set(prow_mask, i);
+    const Mask prow_mask{{(uint64_t)prow32[0] | ((uint64_t)prow32[1] << 32),
+                          (uint64_t)prow32[2] | ((uint64_t)prow32[3] << 32)}};
     // The current frame lives in registers: it is copied in once per pass
     // and written back only when a child is pushed above it (a popped frame is
     // dropped).  Reading and writing its fields in shared memory one by one was
@@ -237,6 +244,7 @@ struct LeafShared {
     int32_t col_of_row[LM], row_of_col[LM];
     int32_t ord_row[LM], ord_col[LM];
     int32_t perm_p[LM], perm_q[LM];
+    uint32_t prow32[LM / 32];            // rows holding a pivot, as bits
     uint32_t dval[LM], inv_d[LM], cval[LM], inv_c[LM];
     Frame stk[MAX_DEPTH];
     unsigned long long step_bar;         // phase k completes when every warp has offered its step-k candidate
@@ -295,6 +303,16 @@ __device__ __forceinline__ uint32_t ff_update(uint32_t d, uint32_t w, uint32_t f
         return reduce32(t + f * (F32.p - q), F32);
     }
     return mul_sub_mul_mod(d, w, f, q, F);
+}
+
+// The phase-1 update d w - f q: for p > 2^16 on residues in Montgomery form
+// (the result stays in that form, one reduction of d w + f (p - q) < 2 p^2)
+template <bool SMALLP>
+__device__ __forceinline__ uint32_t ff_step(uint32_t d, uint32_t w, uint32_t f, uint32_t q,
+                                            const Field &F, const Field32 &F32)
+{
+    if (SMALLP) return ff_update<true>(d, w, f, q, F, F32);
+    return fold(mont_redc((uint64_t)d * w + (uint64_t)f * (F.p - q), F), F.p);
 }
 
 template <bool SMALLP>
@@ -619,7 +637,8 @@ __device__ void leaf_run(LeafShared &S, uint32_t *__restrict__ A, int m, int n, 
 #pragma unroll
         for (int s = 0; s < CPL; ++s) {
             const int j = lane + 32 * s;
-            w[t][s] = (i < m && j < n) ? A[(int64_t)i * lda + j] : 0u;
+            const uint32_t a = (i < m && j < n) ? A[(int64_t)i * lda + j] : 0u;
+            w[t][s] = SMALLP ? a : to_mont(a, F);
         }
     }
     for (int i = tid; i < LM; i += LT) {
@@ -650,6 +669,8 @@ __device__ void leaf_run(LeafShared &S, uint32_t *__restrict__ A, int m, int n, 
     // step waits for every warp's first candidate row, not for all updates.
     // key[(t+1) % 3] is cleared during step t: every read of it happened before
     // the previous phase completed and every write comes after this one.
+    // For p > 2^16 the registers hold Montgomery forms (zero stays zero), and
+    // the pivot values and the staged rows go back to plain residues.
     int r = 0, pi = -1, pc = 0, win = 0;
     uint32_t d = 0;
     bool failed = false;
@@ -672,7 +693,7 @@ __device__ void leaf_run(LeafShared &S, uint32_t *__restrict__ A, int m, int n, 
                 const uint32_t f = __shfl_sync(0xFFFFFFFFu, pick<CPL>(w[t], spc), lpc);
 #pragma unroll
                 for (int s = 0; s < CPL; ++s) {
-                    const uint32_t nv = ff_update<SMALLP>(d, w[t][s], f, prow[s], F, F32);
+                    const uint32_t nv = ff_step<SMALLP>(d, w[t][s], f, prow[s], F, F32);
                     w[t][s] = (s < ncl && ((live >> s) & 1)) ? nv : w[t][s];
                 }
             }
@@ -712,7 +733,7 @@ __device__ void leaf_run(LeafShared &S, uint32_t *__restrict__ A, int m, int n, 
         if (tid == 0) {
             S.piv_row[r] = pi;
             S.piv_col[r] = pc;
-            S.dval[r] = d;
+            S.dval[r] = SMALLP ? d : from_mont(d, F);
             S.col_of_row[pi] = pc;
             S.row_of_col[pc] = pi;
         }
@@ -763,10 +784,16 @@ __device__ void leaf_run(LeafShared &S, uint32_t *__restrict__ A, int m, int n, 
     // (see order_pivots); otherwise thread 0 runs the quad recursion.
     bool descent = false;
     for (int t = tid; t + 1 < r; t += LT) descent |= S.piv_col[t] > S.piv_col[t + 1];
+    if (warp < LM / 32) {   // pivot rows as bits, for the quad recursion
+        const int i = 32 * warp + lane;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, i < m && S.col_of_row[i] >= 0);
+        if (lane == 0) S.prow32[warp] = b;
+    }
     descent = __syncthreads_or(descent);
     if (descent) {
         if (tid == 0) {
-            const int cnt = order_pivots(S.stk, S.col_of_row, S.row_of_col, m, n, S.ord_row, S.ord_col);
+            const int cnt = order_pivots(S.stk, S.col_of_row, S.row_of_col, S.prow32, m, n,
+                                         S.ord_row, S.ord_col);
             int same = cnt == r ? 1 : -1;
             if (same > 0)
                 for (int t = 0; t < r; ++t)
@@ -853,7 +880,8 @@ __device__ void leaf_run(LeafShared &S, uint32_t *__restrict__ A, int m, int n, 
         const int i = warp + NW * t;
         if (i < m) {
 #pragma unroll
-            for (int s = 0; s < CPL; ++s) S.W[i * LD + lane + 32 * s] = w[t][s];
+            for (int s = 0; s < CPL; ++s)
+                S.W[i * LD + lane + 32 * s] = SMALLP ? w[t][s] : from_mont(w[t][s], F);
         }
     }
     // ---------------- fix-up: divide U rows by c_k, L columns by d_k ------
@@ -928,6 +956,86 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
 // the host uses it only below rank-deficient nodes.  Every helper ends with a
 // block-wide barrier, so each step sees the previous one complete.
 
+constexpr int NMAX = 4 * LM;   // largest node side (two levels above the leaves)
+constexpr int SMW = 16384;     // words of the base case's staging area a product borrows
+static_assert(SMW <= LM * LD, "product scratch must fit the leaf staging area");
+constexpr int MT = 64;         // output tile side of the staged products
+constexpr int MKC = 64;        // K chunk of the staged products
+constexpr int MNB = 16;        // staging loads per thread and K chunk
+static_assert(2 * MT * MKC <= SMW && LT * MNB == 2 * MT * MKC, "one staging pass per K chunk");
+constexpr int MM_TILED_K = 16; // shallower products read their operands directly
+
+// C (M x N) <- C - A B over MT x MT output tiles, for products deep enough
+// (K >= MM_TILED_K) that staging pays.  A thread holds a 4 x 2 patch of a tile
+// (rows 4 w + a for warp w, columns lane + 32 b) as delayed-reduction sums;
+// the tile's rows of A and columns of B pass through the shared scratch `sm`
+// MKC at a time, and C is read once per tile.
+template <bool SMALLP>
+__device__ __noinline__ void nd_mm_sub_tiled(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                                       const uint32_t *B, int64_t ldb, int M, int N, int K,
+                                       const Field F, uint32_t *sm)
+{
+    if (M > 0 && N > 0 && K > 0) {
+        const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+        uint32_t *As = sm, *Bs = sm + MT * MKC;   // [MT][MKC], [MKC][MT]
+        const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+        static_assert(NW * 4 == MT && 64 == MT, "thread patches must tile the output tile");
+        for (int i0 = 0; i0 < M; i0 += MT)
+            for (int j0 = 0; j0 < N; j0 += MT) {
+                const int tm = min(MT, M - i0), tn = min(MT, N - j0);
+                uint32_t c[4][2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+                        if (4 * w + a < tm && lane + 32 * b < tn)
+                            c[a][b] = C[(int64_t)(i0 + 4 * w + a) * ldc + j0 + lane + 32 * b];
+                LAcc<SMALLP> acc[4][2];
+                for (int l0 = 0; l0 < K; l0 += MKC) {
+                    const int kc = min(MKC, K - l0);
+                    // tile rows of A (tm x kc, in a MT x MKC frame) and columns of B
+                    // (kc x tn, in a MKC x MT frame): one pass of NB loads per thread
+                                        uint32_t v[MNB];
+#pragma unroll
+                    for (int b = 0; b < MNB; ++b) {
+                        const int e = tid + b * LT;
+                        if (b < MNB / 2) {
+                            const int i = e / MKC, l = e % MKC;
+                            v[b] = i < tm && l < kc ? A[(int64_t)(i0 + i) * lda + l0 + l] : 0u;
+                        } else {
+                            const int l = (e - MT * MKC) / MT, j = (e - MT * MKC) % MT;
+                            v[b] = l < kc && j < tn ? B[(int64_t)(l0 + l) * ldb + j0 + j] : 0u;
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < MNB; ++b) sm[tid + b * LT] = v[b];
+                    __syncthreads();
+#pragma unroll 4
+                    for (int l = 0; l < kc; ++l) {
+                        uint32_t x[4], y[2];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) x[a] = As[(4 * w + a) * MKC + l];
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) y[b] = Bs[l * MT + lane + 32 * b];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) acc[a][b].add(x[a], y[b]);
+                    }
+                    __syncthreads();
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+                        if (4 * w + a < tm && lane + 32 * b < tn)
+                            C[(int64_t)(i0 + 4 * w + a) * ldc + j0 + lane + 32 * b] =
+                                sub_mod(c[a][b], acc[a][b].value(F, w16), F.p);
+            }
+    }
+    __syncthreads();
+}
+
 // X (rows x cols, stride ld) <- X[rmap[i]][cmap[j]] (a null map is the
 // identity), through the global staging area `stage`
 __device__ void nd_perm(uint32_t *X, int64_t ld, int rows, int cols, const int32_t *rmap,
@@ -998,11 +1106,17 @@ __device__ void nd_trsm_right(const uint32_t *U, int64_t ldu, uint32_t *B, int64
 }
 
 // C (M x N) <- C - A B, A M x K, B K x N: each output one delayed reduction
+// (products with K >= MM_TILED_K go through nd_mm_sub_tiled)
 template <bool SMALLP>
 __device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
-                          const uint32_t *B, int64_t ldb, int M, int N, int K, const Field &F)
+                          const uint32_t *B, int64_t ldb, int M, int N, int K, const Field &F,
+                          uint32_t *sm)
 {
     if (M <= 0 || N <= 0 || K <= 0) return;
+    if (K >= MM_TILED_K) {
+        nd_mm_sub_tiled<SMALLP>(C, ldc, A, lda, B, ldb, M, N, K, F, sm);
+        return;
+    }
     const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
     const int tot = M * N;
     for (int e = threadIdx.x; e < tot; e += LT) {
@@ -1013,8 +1127,6 @@ __device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t l
     }
     __syncthreads();
 }
-
-constexpr int NMAX = 4 * LM;   // largest node side (two levels above the leaves)
 
 // Per-level state of a node step: the permutations of its four blocks, the
 // maps of S and T, and each block's r / P identity / Q identity.  A step of
@@ -1133,8 +1245,8 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     // D <- L1^{-1} B1 ; E <- C1 U1^{-1} ; [F;H] <- [B2;A4] - [M1;E] D ; G <- C2 - E V1
     nd_trsm_left<SMALLP>(A, lda, at(0, h), lda, r1, n - h, F);
     nd_trsm_right<SMALLP>(A, lda, at(k, 0), lda, m - k, r1, F, NS.dinv);
-    nd_mm_sub<SMALLP>(at(r1, h), lda, at(r1, 0), lda, at(0, h), lda, m - r1, n - h, r1, F);
-    nd_mm_sub<SMALLP>(at(k, r1), lda, at(k, 0), lda, at(0, r1), lda, m - k, h - r1, r1, F);
+    nd_mm_sub<SMALLP>(at(r1, h), lda, at(r1, 0), lda, at(0, h), lda, m - r1, n - h, r1, F, S.W);
+    nd_mm_sub<SMALLP>(at(k, r1), lda, at(k, 0), lda, at(0, r1), lda, m - k, h - r1, r1, F, S.W);
     // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
     child(1, at(r1, h), k - r1, n - h, tg);
     child(2, at(k, r1), m - k, h - r1, tg);
@@ -1158,12 +1270,12 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     if (r3 > 0 && r2 > 0) nd_copy(a.icopy, r2, at(k, h), lda, r3, r2);
     nd_trsm_left<SMALLP>(at(k, r1), lda, at(k, h), lda, r3, n - h, F);
     // O <- N - J V2 ; R <- H4 - K V2 ; I back ; R <- R - M3 O
-    nd_mm_sub<SMALLP>(at(k, h + r2), lda, at(k, h), lda, at(r1, h + r2), lda, r3, n - h - r2, r2, F);
+    nd_mm_sub<SMALLP>(at(k, h + r2), lda, at(k, h), lda, at(r1, h + r2), lda, r3, n - h - r2, r2, F, S.W);
     nd_mm_sub<SMALLP>(at(k + r3, h + r2), lda, at(k + r3, h), lda, at(r1, h + r2), lda, m - k - r3,
-                      n - h - r2, r2, F);
+                      n - h - r2, r2, F, S.W);
     if (r3 > 0 && r2 > 0) nd_copy(at(k, h), lda, a.icopy, r2, r3, r2);
     nd_mm_sub<SMALLP>(at(k + r3, h + r2), lda, at(k + r3, r1), lda, at(k, h + r2), lda, m - k - r3,
-                      n - h - r2, r3, F);
+                      n - h - r2, r3, F, S.W);
     // R = P4 [L4;M4][U4 V4] Q4
     child(3, at(k + r3, h + r2), m - k - r3, n - h - r2, tg);
     const int r4 = N.info[3][0];

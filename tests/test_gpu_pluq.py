@@ -145,6 +145,7 @@ def test_node_kernel_matches_oracle(p, node):
         cases = [W.planted(256, 256, 60, p, 1)[0], W.planted(300, 200, 150, p, 2)[0],
                  W.planted(700, 500, 120, p, 3)[0], W.planted(520, 900, 400, p, 4)[0],
                  W.planted(400, 400, 200, p, 5, pivot_rows=W.clustered_rows(400, 200, 100, 6))[0],
+                 W.planted(1024, 1000, 990, p, 7)[0],       # nodes whose blocks are nearly full rank
                  (g.integers(0, p, (600, 450)) * (g.random((600, 450)) < 0.01)).astype(np.uint32)]
         X = g.integers(0, p, (640, 40)).astype(np.int64)
         Y = g.integers(0, p, (40, 610)).astype(np.int64)
