@@ -309,6 +309,7 @@ def tune_for(cfg, m, n, p):
     pluq.pluq_set_lazy_zero_test(bool(tuned[3]))
     pluq.pluq_set_leaf_variant(bool(tuned[4]))
     pluq.pluq_set_node_kernel(int(tuned[5]))
+    pluq.pluq_set_node_cluster(int(tuned[6]))
     return tuned
 
 
@@ -342,7 +343,7 @@ def time_single(cfg, mm, steps, warmup, dev, flush):
            "recipe": cfg.note,
            "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1], "branch_min": tuned[2],
                       "lazy_zero_test": tuned[3], "leaf_left_looking": tuned[4],
-                      "node_kernel": tuned[5]}}
+                      "node_kernel": tuned[5], "node_ctas": tuned[6]}}
     if cfg.r is not None:
         out["rank_equals_planted"] = r == cfg.r
     del A, A0, ws
@@ -708,11 +709,13 @@ def run_ours(args):
                        "tuning": {"leaf": tuned[0], "small_mm_macs": tuned[1],
                                   "branch_min": tuned[2], "lazy_zero_test": tuned[3],
                                   "leaf_left_looking": tuned[4], "node_kernel": tuned[5],
+                                  "node_ctas": tuned[6],
                                   "source": "autotune, one knob at a time: leaf {32,64,128}, "
                                             "small-product threshold {2^24,2^25,2^27}, "
                                             "branch threshold {32,64,128,off}, zero test "
                                             "{awaited,lazy}, base case {right,left}-looking, "
-                                            "node kernel levels {1,2,0}"}},
+                                            "node kernel levels {1,2,0}, node kernel "
+                                            "thread blocks {1,2}"}},
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,

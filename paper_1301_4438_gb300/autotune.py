@@ -9,8 +9,9 @@ or rank-deficient) the tuner times `pluq_mod_p` on a seeded synthetic matrix
 of that class, one knob at a time from the defaults (leaf size, then
 small-product threshold, the size above which PLUQ(G) runs on another host
 thread, whether zero tests below rank-deficient nodes are awaited or read
-lazily, the right- or left-looking base case, then whether small nodes below
-rank-deficient ones run in one thread block), and caches the fastest setting
+lazily, the right- or left-looking base case, whether small nodes below
+rank-deficient ones run in one thread block, then whether such a node kernel
+runs as one thread block or a cluster of two), and caches the fastest setting
 in a JSON file.  `apply()` looks
 the class up and sets the library's process-wide knobs.
 """
@@ -31,8 +32,9 @@ BRANCH = (32, 64, 128, 1 << 40)          # 2^40: never hand G to another thread
 LAZY_ZERO = (0, 1)
 LEAF_LEFT = (0, 1)                       # base case right- / left-looking
 NODE = (1, 2, 0)                         # device-side levels of small deficient nodes
-DEFAULT = (128, 1 << 25, 64, 0, 0, 1)
-KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT, NODE)
+NODE_CTAS = (1, 2)                       # thread blocks of a node kernel
+DEFAULT = (128, 1 << 25, 64, 0, 0, 1, 1)
+KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT, NODE, NODE_CTAS)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pluq_gb300", "tuning.json")
 
 
@@ -70,13 +72,15 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
          cache: str = DEFAULT_CACHE, budget_s: float = 60.0, force: bool = False):
     """Time the candidates on one sample of the class, one knob at a time, and
     cache the best; a class already in the cache is returned as cached unless
-    `force`.  Returns (leaf, small_mm_macs, branch_min, lazy_zero, leaf_left, node, ms)."""
+    `force`.  Returns (leaf, small_mm_macs, branch_min, lazy_zero, leaf_left, node,
+    node_ctas, ms)."""
     key = _class_key(m, n, p, deficient)
     if not force:
         ent = _load(cache).get(key)
-        if ent and "node" in ent:
+        if ent and "node_ctas" in ent:
             return (int(ent["leaf"]), int(ent["small_mm_macs"]), int(ent["branch_min"]),
-                    int(ent["lazy_zero"]), int(ent["leaf_left"]), int(ent["node"]), ent["ms"])
+                    int(ent["lazy_zero"]), int(ent["leaf_left"]), int(ent["node"]),
+                    int(ent["node_ctas"]), ent["ms"])
     A0 = _sample(m, n, p, deficient)
     ws = torch.empty(pluq.pluq_workspace_size(m, n, p), dtype=torch.uint8, device="cuda")
     old = pluq.pluq_get_tuning()
@@ -84,6 +88,7 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
     old_lazy = pluq.pluq_get_lazy_zero_test()
     old_left = pluq.pluq_get_leaf_variant()
     old_node = pluq.pluq_get_node_kernel()
+    old_ctas = pluq.pluq_get_node_cluster()
     t_start = time.perf_counter()
 
     def run(cand):
@@ -92,6 +97,7 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
         pluq.pluq_set_lazy_zero_test(bool(cand[3]))
         pluq.pluq_set_leaf_variant(bool(cand[4]))
         pluq.pluq_set_node_kernel(int(cand[5]))
+        pluq.pluq_set_node_cluster(int(cand[6]))
         times = []
         for _ in range(reps + 1):
             A = A0.clone()
@@ -121,11 +127,13 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
         pluq.pluq_set_lazy_zero_test(old_lazy)
         pluq.pluq_set_leaf_variant(old_left)
         pluq.pluq_set_node_kernel(old_node)
+        pluq.pluq_set_node_cluster(old_ctas)
     data = _load(cache)
     data[key] = {"leaf": best[0], "small_mm_macs": best[1], "branch_min": best[2],
-                 "lazy_zero": best[3], "leaf_left": best[4], "node": best[5], "ms": best_ms}
+                 "lazy_zero": best[3], "leaf_left": best[4], "node": best[5],
+                 "node_ctas": best[6], "ms": best_ms}
     _store(cache, data)
-    return best[0], best[1], best[2], best[3], best[4], best[5], best_ms
+    return best[0], best[1], best[2], best[3], best[4], best[5], best[6], best_ms
 
 
 def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_CACHE) -> bool:
@@ -142,4 +150,6 @@ def apply(m: int, n: int, p: int, deficient: bool = False, cache: str = DEFAULT_
         pluq.pluq_set_leaf_variant(bool(ent["leaf_left"]))
     if "node" in ent:
         pluq.pluq_set_node_kernel(int(ent["node"]))
+    if "node_ctas" in ent:
+        pluq.pluq_set_node_cluster(int(ent["node_ctas"]))
     return True

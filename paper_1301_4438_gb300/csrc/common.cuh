@@ -400,5 +400,6 @@ extern std::atomic<bool> g_tune_leaf_left;
 // nodes below rank-deficient ones of at most 2 levels x 2 x leaf on a side go
 // to the node kernel (0: none)
 extern std::atomic<int> g_tune_node;
+extern std::atomic<int> g_tune_node_ctas;   // thread blocks of a node kernel (1 or 2)
 
 }  // namespace pluq

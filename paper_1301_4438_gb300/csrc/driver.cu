@@ -44,6 +44,7 @@ std::atomic<int64_t> g_tune_branch{64};
 std::atomic<int64_t> g_wait_limit{-1};
 std::atomic<bool> g_tune_leaf_left{false};
 std::atomic<int> g_tune_node{1};
+std::atomic<int> g_tune_node_ctas{1};
 // zero test of a block below a rank-deficient node: false = wait for it before
 // descending (a zero block costs one round trip), true = read it with the first
 // leaf of the descent (a nonzero block costs nothing extra)
@@ -856,6 +857,15 @@ pluq_status pluq_set_node_kernel(int levels)
 }
 
 int pluq_get_node_kernel(void) { return g_tune_node.load(); }
+
+pluq_status pluq_set_node_cluster(int ctas)
+{
+    if (ctas != 1 && ctas != 2) return PLUQ_EINVAL;
+    g_tune_node_ctas.store(ctas);
+    return PLUQ_OK;
+}
+
+int pluq_get_node_cluster(void) { return g_tune_node_ctas.load(); }
 
 pluq_status pluq_set_wait_limit(int64_t tries)
 {

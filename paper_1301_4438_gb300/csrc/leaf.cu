@@ -948,13 +948,15 @@ __global__ void __launch_bounds__(LT) leaf_kernel(uint32_t *__restrict__ A, int 
 
 // ------------------------------------------------------------ node kernel --
 // One step of Algorithm 1 on a node whose four blocks A1, F, G, R are base
-// cases (both sides at most twice the leaf size), run by one thread block:
-// the leaves through leaf_run, the permutations, triangular solves and
-// products between them by the whole block on data that stays in L2.  It
-// replaces a dozen launches and four host round trips by one of each, which
-// pays where the blocks have few pivots (deep in a rank-deficient matrix);
-// the host uses it only below rank-deficient nodes.  Every helper ends with a
-// block-wide barrier, so each step sees the previous one complete.
+// cases (both sides at most twice the leaf size), run by one thread block or
+// a cluster of two: the leaves through leaf_run, the permutations, triangular
+// solves and products between them by all threads on data that stays in L2.
+// It replaces a dozen launches and four host round trips by one of each,
+// which pays where the blocks have few pivots (deep in a rank-deficient
+// matrix); the host uses it only below rank-deficient nodes.  In a cluster, F
+// and G (independent, Sec. 2) run at once on the two blocks.  Each phase ends
+// with a barrier over all the node's threads, so it sees the previous one
+// complete.
 
 constexpr int NMAX = 4 * LM;   // largest node side (two levels above the leaves)
 constexpr int SMW = 16384;     // words of the base case's staging area a product borrows
@@ -1036,65 +1038,139 @@ __device__ __noinline__ void nd_mm_sub_tiled(uint32_t *C, int64_t ldc, const uin
     __syncthreads();
 }
 
-// X (rows x cols, stride ld) <- X[rmap[i]][cmap[j]] (a null map is the
-// identity), through the global staging area `stage`
-__device__ void nd_perm(uint32_t *X, int64_t ld, int rows, int cols, const int32_t *rmap,
-                        const int32_t *cmap, uint32_t *stage)
+// The thread blocks of a node kernel: one (NC = 1), or a cluster of NC on as
+// many SMs.  Each helper below does this CTA's share of a phase (rows or
+// columns, or whole elements, split evenly by rank) and sets no barrier; the
+// node step ends every phase with sync(), a block barrier for NC = 1 and a
+// cluster barrier (release / acquire, which also orders global memory)
+// otherwise.  Every CTA executes the same sequence of sync() calls: the only
+// branches around them depend on data that all CTAs hold (sizes, and ranks
+// and identity flags copied to every CTA after each base case).
+template <int NC>
+struct Grp {
+    int rank;
+    __device__ __forceinline__ void range(int tot, int &lo, int &hi) const
+    {
+        lo = (int)((int64_t)tot * rank / NC);
+        hi = (int)((int64_t)tot * (rank + 1) / NC);
+    }
+    __device__ __forceinline__ void sync() const
+    {
+        if constexpr (NC == 1) {
+            __syncthreads();
+        } else {
+            asm volatile("barrier.cluster.arrive.release;\n\t"
+                         "barrier.cluster.wait.acquire;" ::: "memory");
+        }
+    }
+};
+
+__device__ __forceinline__ int cluster_rank()
 {
-    if (rows <= 0 || cols <= 0 || (!rmap && !cmap)) return;
-    const int tot = rows * cols;
-    for (int e = threadIdx.x; e < tot; e += LT) {
-        const int i = e / cols, j = e - (e / cols) * cols;
-        stage[e] = X[(int64_t)(rmap ? rmap[i] : i) * ld + (cmap ? cmap[j] : j)];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < tot; e += LT) {
-        const int i = e / cols, j = e - (e / cols) * cols;
-        X[(int64_t)i * ld + j] = stage[e];
-    }
-    __syncthreads();
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
 }
 
-// dst (rows x cols) <- src
-__device__ void nd_copy(uint32_t *dst, int64_t ldd, const uint32_t *src, int64_t lds, int rows,
-                        int cols)
+// the word at `local` in this CTA's shared memory, in CTA `peer` of the cluster
+__device__ __forceinline__ void st_peer(const void *local, int peer, int32_t v)
 {
-    const int tot = rows * cols;
-    for (int e = threadIdx.x; e < tot; e += LT) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_addr(local)), "r"(peer));
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote), "r"(v) : "memory");
+}
+
+// one permutation of a phase: X (rows x cols, stride ld) <- X[rmap[i]][cmap[j]]
+// (a null map is the identity)
+struct NdPerm {
+    uint32_t *X;
+    int rows, cols;
+    const int32_t *rmap, *cmap;
+};
+
+// The permutations of a phase, on disjoint blocks, through disjoint slices of
+// the global area `stage`: every block is gathered, then (after one barrier)
+// copied back.  Ends with its own barrier; none if no block moves.
+template <int NC>
+__device__ void nd_perms(const NdPerm *ops, int count, int64_t ld, uint32_t *stage, const Grp<NC> &g)
+{
+    bool any = false;
+    int64_t off = 0;
+    for (int o = 0; o < count; ++o) {
+        const NdPerm &q = ops[o];
+        if (q.rows <= 0 || q.cols <= 0 || (!q.rmap && !q.cmap)) continue;
+        any = true;
+        int lo, hi;
+        g.range(q.rows * q.cols, lo, hi);
+        for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
+            const int i = e / q.cols, j = e - (e / q.cols) * q.cols;
+            stage[off + e] = q.X[(int64_t)(q.rmap ? q.rmap[i] : i) * ld + (q.cmap ? q.cmap[j] : j)];
+        }
+        off += (int64_t)q.rows * q.cols;
+    }
+    if (!any) return;
+    g.sync();
+    off = 0;
+    for (int o = 0; o < count; ++o) {
+        const NdPerm &q = ops[o];
+        if (q.rows <= 0 || q.cols <= 0 || (!q.rmap && !q.cmap)) continue;
+        int lo, hi;
+        g.range(q.rows * q.cols, lo, hi);
+        for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
+            const int i = e / q.cols, j = e - (e / q.cols) * q.cols;
+            q.X[(int64_t)i * ld + j] = stage[off + e];
+        }
+        off += (int64_t)q.rows * q.cols;
+    }
+    g.sync();
+}
+
+// dst (rows x cols) <- src, this CTA's share of the elements
+template <int NC>
+__device__ void nd_copy(uint32_t *dst, int64_t ldd, const uint32_t *src, int64_t lds, int rows,
+                        int cols, const Grp<NC> &g)
+{
+    int lo, hi;
+    g.range(rows * cols, lo, hi);
+    for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
         const int i = e / cols, j = e - (e / cols) * cols;
         dst[(int64_t)i * ldd + j] = src[(int64_t)i * lds + j];
     }
-    __syncthreads();
 }
 
-// B (r x N) <- L^{-1} B, L unit lower (diagonal not read): a thread per column,
-// each unknown one delayed-reduction dot product over the earlier ones
-template <bool SMALLP>
+// B (r x N) <- L^{-1} B, L unit lower (diagonal not read): a thread per column
+// of this CTA's share, each unknown one delayed-reduction dot product over the
+// earlier ones
+template <bool SMALLP, int NC>
 __device__ void nd_trsm_left(const uint32_t *L, int64_t ldl, uint32_t *B, int64_t ldb, int r, int N,
-                             const Field &F)
+                             const Field &F, const Grp<NC> &g)
 {
+    if (r <= 1 || N <= 0) return;
     const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    if (r > 1)
-        for (int j = threadIdx.x; j < N; j += LT)
-            for (int i = 1; i < r; ++i) {
-                LAcc<SMALLP> acc;
-                for (int l = 0; l < i; ++l) acc.add(L[(int64_t)i * ldl + l], B[(int64_t)l * ldb + j]);
-                B[(int64_t)i * ldb + j] = sub_mod(B[(int64_t)i * ldb + j], acc.value(F, w16), F.p);
-            }
-    __syncthreads();
+    int lo, hi;
+    g.range(N, lo, hi);
+    for (int j = lo + (int)threadIdx.x; j < hi; j += LT)
+        for (int i = 1; i < r; ++i) {
+            LAcc<SMALLP> acc;
+            for (int l = 0; l < i; ++l) acc.add(L[(int64_t)i * ldl + l], B[(int64_t)l * ldb + j]);
+            B[(int64_t)i * ldb + j] = sub_mod(B[(int64_t)i * ldb + j], acc.value(F, w16), F.p);
+        }
 }
 
-// B (M x r) <- B U^{-1}, U upper with nonzero diagonal: a thread per row;
-// dinv (r words of shared memory) receives the inverses of the diagonal
-template <bool SMALLP>
+// B (M x r) <- B U^{-1}, U upper with nonzero diagonal: a thread per row of
+// this CTA's share; dinv (r words of this CTA's shared memory) receives the
+// inverses of the diagonal
+template <bool SMALLP, int NC>
 __device__ void nd_trsm_right(const uint32_t *U, int64_t ldu, uint32_t *B, int64_t ldb, int M, int r,
-                              const Field &F, uint32_t *dinv)
+                              const Field &F, uint32_t *dinv, const Grp<NC> &g)
 {
     if (r <= 0 || M <= 0) return;
     const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
     for (int t = threadIdx.x; t < r; t += LT) dinv[t] = inv_mod(U[(int64_t)t * ldu + t], F.p);
     __syncthreads();
-    for (int i = threadIdx.x; i < M; i += LT) {
+    int lo, hi;
+    g.range(M, lo, hi);
+    for (int i = lo + (int)threadIdx.x; i < hi; i += LT) {
         uint32_t *row = B + (int64_t)i * ldb;
         for (int j = 0; j < r; ++j) {
             LAcc<SMALLP> acc;
@@ -1102,16 +1178,21 @@ __device__ void nd_trsm_right(const uint32_t *U, int64_t ldu, uint32_t *B, int64
             row[j] = mul_mod(sub_mod(row[j], acc.value(F, w16), F.p), dinv[j], F);
         }
     }
-    __syncthreads();
 }
 
-// C (M x N) <- C - A B, A M x K, B K x N: each output one delayed reduction
-// (products with K >= MM_TILED_K go through nd_mm_sub_tiled)
-template <bool SMALLP>
+// C (M x N) <- C - A B, A M x K, B K x N, this CTA's share of the rows: each
+// output one delayed reduction, or (K >= MM_TILED_K) through nd_mm_sub_tiled;
+// ends with a block barrier where it ran
+template <bool SMALLP, int NC>
 __device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
                           const uint32_t *B, int64_t ldb, int M, int N, int K, const Field &F,
-                          uint32_t *sm)
+                          uint32_t *sm, const Grp<NC> &g)
 {
+    int lo, hi;
+    g.range(M, lo, hi);
+    C += (int64_t)lo * ldc;
+    A += (int64_t)lo * lda;
+    M = hi - lo;
     if (M <= 0 || N <= 0 || K <= 0) return;
     if (K >= MM_TILED_K) {
         nd_mm_sub_tiled<SMALLP>(C, ldc, A, lda, B, ldb, M, N, K, F, sm);
@@ -1128,6 +1209,8 @@ __device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t l
     __syncthreads();
 }
 
+constexpr int NCMAX = 2;   // largest cluster of a node kernel
+
 // Per-level state of a node step: the permutations of its four blocks, the
 // maps of S and T, and each block's r / P identity / Q identity.  A step of
 // level l has blocks of sides up to (l == 1 ? LM : 2 LM).
@@ -1142,7 +1225,44 @@ struct NodeShared {
     NodeLevel<LM> l1;
     NodeLevel<2 * LM> l2;
     uint32_t dinv[2 * LM];
+    int32_t flags[NCMAX];      // the CTAs' zero-test results
 };
+
+// true if some entry of X (rows x cols) is nonzero; every CTA gets the answer
+template <int NC>
+__device__ bool nd_any_nonzero(const uint32_t *X, int64_t ld, int rows, int cols, int32_t *flags,
+                               const Grp<NC> &g)
+{
+    int lo, hi;
+    g.range(rows * cols, lo, hi);
+    bool nz = false;
+    for (int e = lo + (int)threadIdx.x; e < hi && !nz; e += LT)
+        nz = X[(int64_t)(e / cols) * ld + (e - (e / cols) * cols)] != 0;
+    const bool mine = __syncthreads_or(nz);
+    if constexpr (NC == 1) {
+        return mine;
+    } else {
+        if ((int)threadIdx.x < NC) st_peer(&flags[g.rank], threadIdx.x, mine ? 1 : 0);
+        g.sync();
+        int any = 0;
+        for (int c = 0; c < NC; ++c) any |= flags[c];
+        g.sync();   // every CTA has read the flags before any is written again
+        return any != 0;
+    }
+}
+
+// the P, Q and info of block c, computed by this CTA, into the other CTAs'
+// copies of the level state
+template <int NC, int V>
+__device__ void push_child(NodeLevel<V> &N, int c, int mb, int nb, const Grp<NC> &g)
+{
+    for (int peer = 0; peer < NC; ++peer) {
+        if (peer == g.rank) continue;
+        for (int i = threadIdx.x; i < mb; i += LT) st_peer(&N.pv[2 * c][i], peer, N.pv[2 * c][i]);
+        for (int j = threadIdx.x; j < nb; j += LT) st_peer(&N.pv[2 * c + 1][j], peer, N.pv[2 * c + 1][j]);
+        if (threadIdx.x < 3) st_peer(&N.info[c][threadIdx.x], peer, N.info[c][threadIdx.x]);
+    }
+}
 
 struct NodeArgs {
     uint32_t *A;
@@ -1178,14 +1298,15 @@ __device__ __forceinline__ auto &node_level(NodeShared &N)
 }
 
 // One step of Algorithm 1 on the m x n block at A (both sides at most 2^LEVEL
-// LM) by the whole thread block: blocks that are base cases go to
-// leaf_run_full, larger ones (LEVEL 2) to a step of level 1.  Writes P / Q to
+// LM) by the NC thread blocks: blocks that are base cases go to leaf_run_full
+// on one CTA (F and G on different CTAs when NC > 1, so they run at once),
+// larger ones (LEVEL 2) to a step of level 1 on all CTAs.  Writes P / Q to
 // pp / pq and r, P identity, Q identity to info[0..2] (-1 for r if a base
-// case gave up a bounded wait).
-template <bool SMALLP, int LEVEL>
+// case gave up a bounded wait); every CTA writes the same values.
+template <bool SMALLP, int LEVEL, int NC>
 __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const NodeArgs &a,
                                        uint32_t *A, int m, int n, int32_t *pp, int32_t *pq,
-                                       int32_t *info, int try_generic)
+                                       int32_t *info, int try_generic, const Grp<NC> g)
 {
     auto &N = node_level<LEVEL>(NS);
     const int tid = threadIdx.x;
@@ -1201,8 +1322,10 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
         }
         __syncthreads();
     };
-    // block c (0 A1, 1 F, 2 G, 3 R); an empty block has r = 0, P = Q = I
-    auto child = [&](int c, uint32_t *X, int mb, int nb, int tg) {
+    // block c (0 A1, 1 F, 2 G, 3 R); an empty block has r = 0, P = Q = I.  A
+    // base case runs on CTA `owner`, which then copies its results to the
+    // others; no barrier here, the caller ends the phase
+    auto child = [&](int c, uint32_t *X, int mb, int nb, int tg, int owner) {
         if (mb <= 0 || nb <= 0) {
             if (tid == 0) {
                 N.info[c][0] = 0;
@@ -1210,27 +1333,31 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
                 N.info[c][2] = 1;
             }
         } else if (mb <= LM && nb <= LM) {
-            leaf_run_full<SMALLP>(S, X, mb, nb, lda, F, N.pv[2 * c], N.pv[2 * c + 1], N.info[c],
-                                  tg, a.wait_limit, a.left_looking);
+            if (g.rank == owner) {
+                leaf_run_full<SMALLP>(S, X, mb, nb, lda, F, N.pv[2 * c], N.pv[2 * c + 1], N.info[c],
+                                      tg, a.wait_limit, a.left_looking);
+                if constexpr (NC > 1) {
+                    __syncthreads();
+                    push_child<NC>(N, c, mb, nb, g);
+                }
+            }
         } else {
             if constexpr (LEVEL > 1)
-                node_step<SMALLP, LEVEL - 1>(S, NS, a, X, mb, nb, N.pv[2 * c], N.pv[2 * c + 1],
-                                             N.info[c], tg);
+                node_step<SMALLP, LEVEL - 1, NC>(S, NS, a, X, mb, nb, N.pv[2 * c], N.pv[2 * c + 1],
+                                                 N.info[c], tg, g);
         }
-        __syncthreads();
     };
 
     // a zero block is finished: r = 0, P = Q = I
-    bool nz = false;
-    for (int e = tid; e < m * n && !nz; e += LT) nz = *at(e / n, e % n) != 0;
-    if (!__syncthreads_or(nz)) {
+    if (!nd_any_nonzero<NC>(A, lda, m, n, NS.flags, g)) {
         for (int i = tid; i < m; i += LT) pp[i] = i;
         for (int j = tid; j < n; j += LT) pq[j] = j;
         done(0, 1, 1);
         return;
     }
     // A1 = P1 [L1; M1] [U1 V1] Q1
-    child(0, A, k, h, try_generic);
+    child(0, A, k, h, try_generic, 0);
+    g.sync();
     const int r1 = N.info[0][0];
     if (r1 < 0) {
         done(-1, 0, 0);
@@ -1240,16 +1367,21 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     const int32_t *Q1 = N.info[0][2] ? nullptr : N.pv[1];
     const int tg = r1 < (k < h ? k : h) ? 0 : 1;
     // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
-    nd_perm(at(0, h), lda, k, n - h, P1, nullptr, a.stage);
-    nd_perm(at(k, 0), lda, m - k, h, nullptr, Q1, a.stage);
+    {
+        const NdPerm ops[2] = {{at(0, h), k, n - h, P1, nullptr}, {at(k, 0), m - k, h, nullptr, Q1}};
+        nd_perms<NC>(ops, 2, lda, a.stage, g);
+    }
     // D <- L1^{-1} B1 ; E <- C1 U1^{-1} ; [F;H] <- [B2;A4] - [M1;E] D ; G <- C2 - E V1
-    nd_trsm_left<SMALLP>(A, lda, at(0, h), lda, r1, n - h, F);
-    nd_trsm_right<SMALLP>(A, lda, at(k, 0), lda, m - k, r1, F, NS.dinv);
-    nd_mm_sub<SMALLP>(at(r1, h), lda, at(r1, 0), lda, at(0, h), lda, m - r1, n - h, r1, F, S.W);
-    nd_mm_sub<SMALLP>(at(k, r1), lda, at(k, 0), lda, at(0, r1), lda, m - k, h - r1, r1, F, S.W);
-    // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3
-    child(1, at(r1, h), k - r1, n - h, tg);
-    child(2, at(k, r1), m - k, h - r1, tg);
+    nd_trsm_left<SMALLP, NC>(A, lda, at(0, h), lda, r1, n - h, F, g);
+    nd_trsm_right<SMALLP, NC>(A, lda, at(k, 0), lda, m - k, r1, F, NS.dinv, g);
+    g.sync();
+    nd_mm_sub<SMALLP, NC>(at(r1, h), lda, at(r1, 0), lda, at(0, h), lda, m - r1, n - h, r1, F, S.W, g);
+    nd_mm_sub<SMALLP, NC>(at(k, r1), lda, at(k, 0), lda, at(0, r1), lda, m - k, h - r1, r1, F, S.W, g);
+    g.sync();
+    // F = P2 [L2;M2][U2 V2] Q2 ; G = P3 [L3;M3][U3 V3] Q3, on different CTAs
+    child(1, at(r1, h), k - r1, n - h, tg, 0);
+    child(2, at(k, r1), m - k, h - r1, tg, NC - 1);
+    g.sync();
     const int r2 = N.info[1][0], r3 = N.info[2][0];
     if (r2 < 0 || r3 < 0) {
         done(-1, 0, 0);
@@ -1260,24 +1392,36 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     const int32_t *P3 = N.info[2][1] ? nullptr : N.pv[4];
     const int32_t *Q3 = N.info[2][2] ? nullptr : N.pv[5];
     // H <- P3^T H Q2^T ; E <- P3^T E ; M1 <- P2^T M1 ; D <- D Q2^T ; V1 <- V1 Q3^T
-    nd_perm(at(k, h), lda, m - k, n - h, P3, Q2, a.stage);
-    nd_perm(at(k, 0), lda, m - k, r1, P3, nullptr, a.stage);
-    nd_perm(at(r1, 0), lda, k - r1, r1, P2, nullptr, a.stage);
-    nd_perm(at(0, h), lda, r1, n - h, nullptr, Q2, a.stage);
-    nd_perm(at(0, r1), lda, r1, h - r1, nullptr, Q3, a.stage);
+    {
+        const NdPerm ops[5] = {{at(k, h), m - k, n - h, P3, Q2},
+                               {at(k, 0), m - k, r1, P3, nullptr},
+                               {at(r1, 0), k - r1, r1, P2, nullptr},
+                               {at(0, h), r1, n - h, nullptr, Q2},
+                               {at(0, r1), r1, h - r1, nullptr, Q3}};
+        nd_perms<NC>(ops, 5, lda, a.stage, g);
+    }
     // [I;K] <- [H1;H3] U2^{-1} ; keep I ; [J N] <- L3^{-1} [I H2]
-    nd_trsm_right<SMALLP>(at(r1, h), lda, at(k, h), lda, m - k, r2, F, NS.dinv);
-    if (r3 > 0 && r2 > 0) nd_copy(a.icopy, r2, at(k, h), lda, r3, r2);
-    nd_trsm_left<SMALLP>(at(k, r1), lda, at(k, h), lda, r3, n - h, F);
-    // O <- N - J V2 ; R <- H4 - K V2 ; I back ; R <- R - M3 O
-    nd_mm_sub<SMALLP>(at(k, h + r2), lda, at(k, h), lda, at(r1, h + r2), lda, r3, n - h - r2, r2, F, S.W);
-    nd_mm_sub<SMALLP>(at(k + r3, h + r2), lda, at(k + r3, h), lda, at(r1, h + r2), lda, m - k - r3,
-                      n - h - r2, r2, F, S.W);
-    if (r3 > 0 && r2 > 0) nd_copy(at(k, h), lda, a.icopy, r2, r3, r2);
-    nd_mm_sub<SMALLP>(at(k + r3, h + r2), lda, at(k + r3, r1), lda, at(k, h + r2), lda, m - k - r3,
-                      n - h - r2, r3, F, S.W);
+    nd_trsm_right<SMALLP, NC>(at(r1, h), lda, at(k, h), lda, m - k, r2, F, NS.dinv, g);
+    g.sync();
+    if (r3 > 0 && r2 > 0) {
+        nd_copy<NC>(a.icopy, r2, at(k, h), lda, r3, r2, g);
+        g.sync();
+    }
+    nd_trsm_left<SMALLP, NC>(at(k, r1), lda, at(k, h), lda, r3, n - h, F, g);
+    g.sync();
+    // O <- N - J V2 ; R <- H4 - K V2 ; then I back and R <- R - M3 O
+    nd_mm_sub<SMALLP, NC>(at(k, h + r2), lda, at(k, h), lda, at(r1, h + r2), lda, r3, n - h - r2,
+                          r2, F, S.W, g);
+    nd_mm_sub<SMALLP, NC>(at(k + r3, h + r2), lda, at(k + r3, h), lda, at(r1, h + r2), lda,
+                          m - k - r3, n - h - r2, r2, F, S.W, g);
+    g.sync();
+    if (r3 > 0 && r2 > 0) nd_copy<NC>(at(k, h), lda, a.icopy, r2, r3, r2, g);
+    nd_mm_sub<SMALLP, NC>(at(k + r3, h + r2), lda, at(k + r3, r1), lda, at(k, h + r2), lda,
+                          m - k - r3, n - h - r2, r3, F, S.W, g);
+    g.sync();
     // R = P4 [L4;M4][U4 V4] Q4
-    child(3, at(k + r3, h + r2), m - k - r3, n - h - r2, tg);
+    child(3, at(k + r3, h + r2), m - k - r3, n - h - r2, tg, 0);
+    g.sync();
     const int r4 = N.info[3][0];
     if (r4 < 0) {
         done(-1, 0, 0);
@@ -1286,10 +1430,13 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     const int32_t *P4 = N.info[3][1] ? nullptr : N.pv[6];
     const int32_t *Q4 = N.info[3][2] ? nullptr : N.pv[7];
     // [E2 M3 0 K] <- P4^T [..] ; [D2;V2;0;O] <- [..] Q4^T
-    nd_perm(at(k + r3, 0), lda, m - k - r3, h + r2, P4, nullptr, a.stage);
-    nd_perm(at(0, h + r2), lda, k + r3, n - h - r2, nullptr, Q4, a.stage);
+    {
+        const NdPerm ops[2] = {{at(k + r3, 0), m - k - r3, h + r2, P4, nullptr},
+                               {at(0, h + r2), k + r3, n - h - r2, nullptr, Q4}};
+        nd_perms<NC>(ops, 2, lda, a.stage, g);
+    }
     // P = Diag(P1 diag(I,P2), P3 diag(I,P4)) S, Q = T Diag(diag(I,Q3) Q1, diag(I,Q4) Q2),
-    // and the row map of S / column map of T
+    // and the row map of S / column map of T (every CTA, into its own maps)
     auto ap = [](const int32_t *v, int x) { return v ? v[x] : x; };
     bool s_same = true, t_same = true;
     for (int i = tid; i < m; i += LT) {
@@ -1326,7 +1473,10 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     const bool s_ident = __syncthreads_and(s_same);
     const bool t_ident = __syncthreads_and(t_same);
     // A <- S^T A T^T
-    nd_perm(A, lda, m, n, s_ident ? nullptr : N.smap, t_ident ? nullptr : N.tmap, a.stage);
+    {
+        const NdPerm op{A, m, n, s_ident ? nullptr : N.smap, t_ident ? nullptr : N.tmap};
+        nd_perms<NC>(&op, 1, lda, a.stage, g);
+    }
     int pid = s_ident, qid = t_ident;
     for (int c = 0; c < 4; ++c) {
         pid &= N.info[c][1] != 0;
@@ -1335,14 +1485,24 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     done(r1 + r2 + r3 + r4, pid, qid);
 }
 
-template <bool SMALLP, int LEVEL>
+template <bool SMALLP, int LEVEL, int NC>
 __global__ void __launch_bounds__(LT, 1) node_kernel(const __grid_constant__ NodeArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafShared &S = *reinterpret_cast<LeafShared *>(smem_raw);
     __shared__ NodeShared NS;
-    node_step<SMALLP, LEVEL>(S, NS, a, a.A, a.m, a.n, a.perm_p, a.perm_q, a.info, a.try_generic);
-    if (threadIdx.x == 0 && a.host_info) {
+    Grp<NC> g{0};
+    if constexpr (NC > 1) {
+        g.rank = cluster_rank();
+        g.sync();   // every CTA has started before any writes another's shared memory
+    }
+    node_step<SMALLP, LEVEL, NC>(S, NS, a, a.A, a.m, a.n, a.perm_p, a.perm_q, a.info,
+                                 a.try_generic, g);
+    if constexpr (NC > 1) {
+        __threadfence();
+        g.sync();   // every CTA's writes are done before the result is published
+    }
+    if (g.rank == 0 && threadIdx.x == 0 && a.host_info) {
         a.host_info[1] = a.info[0];
         a.host_info[2] = a.info[1];
         a.host_info[3] = a.info[2];
@@ -1376,17 +1536,43 @@ pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     a.left_looking = g_tune_leaf_left.load(std::memory_order_relaxed) ? 1 : 0;
     const size_t smem = sizeof(LeafShared);
     const bool two = m > 2 * LM || n > 2 * LM;   // blocks larger than base cases
+    const int nc = g_tune_node_ctas.load(std::memory_order_relaxed) > 1 ? 2 : 1;
     prof::start(prof::LEAF, st);
-#define PLUQ_NODE_CASE(SP, LV)                                                                   \
-    {                                                                                            \
-        static std::atomic<uint64_t> attr{0};                                                    \
-        if (!smem_attr_once((const void *)node_kernel<SP, LV>, smem, attr)) return PLUQ_ECUDA;    \
-        node_kernel<SP, LV><<<1, LT, smem, st>>>(a);                                             \
+#define PLUQ_NODE_CASE(SP, LV, NCV)                                                               \
+    {                                                                                             \
+        static std::atomic<uint64_t> attr{0};                                                     \
+        if (!smem_attr_once((const void *)node_kernel<SP, LV, NCV>, smem, attr)) return PLUQ_ECUDA; \
+        if (NCV == 1) {                                                                           \
+            node_kernel<SP, LV, NCV><<<1, LT, smem, st>>>(a);                                     \
+        } else {                                                                                  \
+            cudaLaunchConfig_t cfg = {};                                                          \
+            cfg.gridDim = dim3(NCV, 1, 1);                                                        \
+            cfg.blockDim = dim3(LT, 1, 1);                                                        \
+            cfg.dynamicSmemBytes = smem;                                                          \
+            cfg.stream = st;                                                                      \
+            cudaLaunchAttribute at[1];                                                            \
+            at[0].id = cudaLaunchAttributeClusterDimension;                                       \
+            at[0].val.clusterDim.x = NCV;                                                         \
+            at[0].val.clusterDim.y = 1;                                                           \
+            at[0].val.clusterDim.z = 1;                                                           \
+            cfg.attrs = at;                                                                       \
+            cfg.numAttrs = 1;                                                                     \
+            if (cudaLaunchKernelEx(&cfg, node_kernel<SP, LV, NCV>, a) != cudaSuccess)              \
+                return PLUQ_ECUDA;                                                                \
+        }                                                                                         \
     }
     if (F.p <= 65536u) {
-        if (two) PLUQ_NODE_CASE(true, 2) else PLUQ_NODE_CASE(true, 1)
+        if (nc == 2) {
+            if (two) PLUQ_NODE_CASE(true, 2, 2) else PLUQ_NODE_CASE(true, 1, 2)
+        } else {
+            if (two) PLUQ_NODE_CASE(true, 2, 1) else PLUQ_NODE_CASE(true, 1, 1)
+        }
     } else {
-        if (two) PLUQ_NODE_CASE(false, 2) else PLUQ_NODE_CASE(false, 1)
+        if (nc == 2) {
+            if (two) PLUQ_NODE_CASE(false, 2, 2) else PLUQ_NODE_CASE(false, 1, 2)
+        } else {
+            if (two) PLUQ_NODE_CASE(false, 2, 1) else PLUQ_NODE_CASE(false, 1, 1)
+        }
     }
 #undef PLUQ_NODE_CASE
     pluq_status s = last_launch();

@@ -92,6 +92,8 @@ _SIGS = {
     "pluq_get_leaf_variant": (ctypes.c_int, []),
     "pluq_set_node_kernel": (ctypes.c_int, [ctypes.c_int]),
     "pluq_get_node_kernel": (ctypes.c_int, []),
+    "pluq_set_node_cluster": (ctypes.c_int, [ctypes.c_int]),
+    "pluq_get_node_cluster": (ctypes.c_int, []),
     "pluq_device_status": (ctypes.c_int, [_vp]),
     "pluq_get_lazy_zero_test": (ctypes.c_int, []),
     "pluq_launch_count": (ctypes.c_longlong, []),
@@ -626,3 +628,12 @@ def pluq_set_node_kernel(levels: int):
 
 def pluq_get_node_kernel() -> int:
     return int(load().pluq_get_node_kernel())
+
+
+def pluq_set_node_cluster(ctas: int):
+    """Thread blocks of a node kernel: 1, or a cluster of 2 (speed only)."""
+    _check(load().pluq_set_node_cluster(int(ctas)), "pluq_set_node_cluster")
+
+
+def pluq_get_node_cluster() -> int:
+    return int(load().pluq_get_node_cluster())

@@ -130,17 +130,19 @@ def test_tuning_knobs_do_not_change_results():
     assert np.array_equal(outs[0][0], LU0)
 
 
-@pytest.mark.parametrize("node", [2, 1, 0])
+@pytest.mark.parametrize("node,ctas", [(2, 1), (1, 1), (0, 1), (1, 2), (2, 2)])
 @pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
-def test_node_kernel_matches_oracle(p, node):
+def test_node_kernel_matches_oracle(p, node, ctas):
     """With the node kernel on, nodes of at most twice (levels 1) or four times
     (levels 2) the leaf size below rank-deficient nodes are computed in one
-    thread block; with it off they take the host-driven path.  Either way results stay element-wise equal to
+    thread block, or in a cluster of two (ctas 2: F and G at once, the steps
+    between them split); with it off they take the host-driven path.  Either way results stay element-wise equal to
     the oracle (planted profiles of several densities,
     a clustered profile, sparse and low-rank products, rectangular shapes)."""
     g = np.random.Generator(np.random.PCG64(p + 99))
-    old = pluq.pluq_get_node_kernel()
+    old, old_ctas = pluq.pluq_get_node_kernel(), pluq.pluq_get_node_cluster()
     pluq.pluq_set_node_kernel(node)
+    pluq.pluq_set_node_cluster(ctas)
     try:
         cases = [W.planted(256, 256, 60, p, 1)[0], W.planted(300, 200, 150, p, 2)[0],
                  W.planted(700, 500, 120, p, 3)[0], W.planted(520, 900, 400, p, 4)[0],
@@ -160,3 +162,4 @@ def test_node_kernel_matches_oracle(p, node):
             assert np.array_equal(d.cpu().numpy().astype(np.uint32), LU0), A.shape
     finally:
         pluq.pluq_set_node_kernel(old)
+        pluq.pluq_set_node_cluster(old_ctas)
