@@ -11,7 +11,7 @@ small-product threshold, the size above which PLUQ(G) runs on another host
 thread, whether zero tests below rank-deficient nodes are awaited or read
 lazily, the right- or left-looking base case, whether small nodes below
 rank-deficient ones run in one thread block, then whether such a node kernel
-runs as one thread block or a cluster of two), and caches the fastest setting
+runs as one thread block or a cluster of two or four), and caches the fastest setting
 in a JSON file.  `apply()` looks
 the class up and sets the library's process-wide knobs.
 """
@@ -32,7 +32,7 @@ BRANCH = (32, 64, 128, 1 << 40)          # 2^40: never hand G to another thread
 LAZY_ZERO = (0, 1)
 LEAF_LEFT = (0, 1)                       # base case right- / left-looking
 NODE = (1, 2, 0)                         # device-side levels of small deficient nodes
-NODE_CTAS = (1, 2)                       # thread blocks of a node kernel
+NODE_CTAS = (1, 2, 4)                    # thread blocks of a node kernel
 DEFAULT = (128, 1 << 25, 64, 0, 0, 1, 1)
 KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT, NODE, NODE_CTAS)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pluq_gb300", "tuning.json")

@@ -1038,8 +1038,8 @@ __device__ __noinline__ void nd_mm_sub_tiled(uint32_t *C, int64_t ldc, const uin
     __syncthreads();
 }
 
-// The thread blocks of a node kernel: one (NC = 1), or a cluster of NC on as
-// many SMs.  Each helper below does this CTA's share of a phase (rows or
+// The thread blocks of a node kernel: one (NC = 1), or a cluster of NC = 2
+// or 4 on as many SMs.  Each helper below does this CTA's share of a phase (rows or
 // columns, or whole elements, split evenly by rank) and sets no barrier; the
 // node step ends every phase with sync(), a block barrier for NC = 1 and a
 // cluster barrier (release / acquire, which also orders global memory)
@@ -1209,7 +1209,7 @@ __device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t l
     __syncthreads();
 }
 
-constexpr int NCMAX = 2;   // largest cluster of a node kernel
+constexpr int NCMAX = 4;   // largest cluster of a node kernel
 
 // Per-level state of a node step: the permutations of its four blocks, the
 // maps of S and T, and each block's r / P identity / Q identity.  A step of
@@ -1536,7 +1536,7 @@ pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     a.left_looking = g_tune_leaf_left.load(std::memory_order_relaxed) ? 1 : 0;
     const size_t smem = sizeof(LeafShared);
     const bool two = m > 2 * LM || n > 2 * LM;   // blocks larger than base cases
-    const int nc = g_tune_node_ctas.load(std::memory_order_relaxed) > 1 ? 2 : 1;
+    const int nc = g_tune_node_ctas.load(std::memory_order_relaxed);
     prof::start(prof::LEAF, st);
 #define PLUQ_NODE_CASE(SP, LV, NCV)                                                               \
     {                                                                                             \
@@ -1562,13 +1562,17 @@ pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
         }                                                                                         \
     }
     if (F.p <= 65536u) {
-        if (nc == 2) {
+        if (nc == 4) {
+            if (two) PLUQ_NODE_CASE(true, 2, 4) else PLUQ_NODE_CASE(true, 1, 4)
+        } else if (nc == 2) {
             if (two) PLUQ_NODE_CASE(true, 2, 2) else PLUQ_NODE_CASE(true, 1, 2)
         } else {
             if (two) PLUQ_NODE_CASE(true, 2, 1) else PLUQ_NODE_CASE(true, 1, 1)
         }
     } else {
-        if (nc == 2) {
+        if (nc == 4) {
+            if (two) PLUQ_NODE_CASE(false, 2, 4) else PLUQ_NODE_CASE(false, 1, 4)
+        } else if (nc == 2) {
             if (two) PLUQ_NODE_CASE(false, 2, 2) else PLUQ_NODE_CASE(false, 1, 2)
         } else {
             if (two) PLUQ_NODE_CASE(false, 2, 1) else PLUQ_NODE_CASE(false, 1, 1)
