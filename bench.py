@@ -715,7 +715,7 @@ def run_ours(args):
                                             "branch threshold {32,64,128,off}, zero test "
                                             "{awaited,lazy}, base case {right,left}-looking, "
                                             "node kernel levels {1,2,0}, node kernel "
-                                            "thread blocks {1,2,4}"}},
+                                            "thread blocks {1,2,4,8}"}},
             "roofline": roof,
             "roofline_modular_product": roof_mm,
             "modular_gemm_standalone": gemm_big,

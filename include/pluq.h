@@ -454,7 +454,7 @@ int pluq_get_node_kernel(void);
 
 /*
  * Thread blocks of a node kernel (speed only, never results): 1 (default), or
- * a cluster of 2 or 4 on as many SMs.  In a cluster the two middle base cases
+ * a cluster of 2, 4 or 8 on as many SMs.  In a cluster the two middle base cases
  * of a step (F and G of Algorithm 1, independent of each other) run at once
  * on different blocks, and the permutations, triangular solves and products
  * between the base cases are split over the blocks.  EINVAL for other values.

@@ -9,10 +9,10 @@ or rank-deficient) the tuner times `pluq_mod_p` on a seeded synthetic matrix
 of that class, one knob at a time from the defaults (leaf size, then
 small-product threshold, the size above which PLUQ(G) runs on another host
 thread, whether zero tests below rank-deficient nodes are awaited or read
-lazily, the right- or left-looking base case, whether small nodes below
-rank-deficient ones run in one thread block, then whether such a node kernel
-runs as one thread block or a cluster of two or four), and caches the fastest setting
-in a JSON file.  `apply()` looks
+lazily, the right- or left-looking base case, whether a node kernel (a small
+node below a rank-deficient one in one launch) runs as one thread block or a
+cluster of two, four or eight, then how many levels it covers), and caches
+the fastest setting in a JSON file.  `apply()` looks
 the class up and sets the library's process-wide knobs.
 """
 from __future__ import annotations
@@ -32,9 +32,11 @@ BRANCH = (32, 64, 128, 1 << 40)          # 2^40: never hand G to another thread
 LAZY_ZERO = (0, 1)
 LEAF_LEFT = (0, 1)                       # base case right- / left-looking
 NODE = (1, 2, 0)                         # device-side levels of small deficient nodes
-NODE_CTAS = (1, 2, 4)                    # thread blocks of a node kernel
+NODE_CTAS = (1, 2, 4, 8)                 # thread blocks of a node kernel
 DEFAULT = (128, 1 << 25, 64, 0, 0, 1, 1)
 KNOBS = (LEAVES, SMALL_MM, BRANCH, LAZY_ZERO, LEAF_LEFT, NODE, NODE_CTAS)
+ORDER = (0, 1, 2, 3, 4, 6, 5)            # the cluster size before the node levels: a
+                                         # larger cluster makes deeper node kernels pay
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pluq_gb300", "tuning.json")
 
 
@@ -111,8 +113,8 @@ def tune(m: int, n: int, p: int, deficient: bool = False, reps: int = 2,
     try:
         best = DEFAULT
         best_ms = run(best)
-        for knob, options in enumerate(KNOBS):
-            for v in options:
+        for knob in ORDER:
+            for v in KNOBS[knob]:
                 if time.perf_counter() - t_start > budget_s:
                     break
                 cand = tuple(v if i == knob else best[i] for i in range(len(KNOBS)))

@@ -860,7 +860,7 @@ int pluq_get_node_kernel(void) { return g_tune_node.load(); }
 
 pluq_status pluq_set_node_cluster(int ctas)
 {
-    if (ctas != 1 && ctas != 2 && ctas != 4) return PLUQ_EINVAL;
+    if (ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8) return PLUQ_EINVAL;
     g_tune_node_ctas.store(ctas);
     return PLUQ_OK;
 }

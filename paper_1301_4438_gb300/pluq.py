@@ -631,7 +631,7 @@ def pluq_get_node_kernel() -> int:
 
 
 def pluq_set_node_cluster(ctas: int):
-    """Thread blocks of a node kernel: 1, or a cluster of 2 or 4 (speed only)."""
+    """Thread blocks of a node kernel: 1, or a cluster of 2, 4 or 8 (speed only)."""
     _check(load().pluq_set_node_cluster(int(ctas)), "pluq_set_node_cluster")
 
 

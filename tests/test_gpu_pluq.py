@@ -130,12 +130,12 @@ def test_tuning_knobs_do_not_change_results():
     assert np.array_equal(outs[0][0], LU0)
 
 
-@pytest.mark.parametrize("node,ctas", [(2, 1), (1, 1), (0, 1), (1, 2), (2, 2), (1, 4), (2, 4)])
+@pytest.mark.parametrize("node,ctas", [(2, 1), (1, 1), (0, 1), (1, 2), (2, 2), (1, 4), (2, 4), (1, 8), (2, 8)])
 @pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
 def test_node_kernel_matches_oracle(p, node, ctas):
     """With the node kernel on, nodes of at most twice (levels 1) or four times
     (levels 2) the leaf size below rank-deficient nodes are computed in one
-    thread block, or in a cluster of two or four (F and G at once, the steps
+    thread block, or in a cluster of 2, 4 or 8 (F and G at once, the steps
     between them split); with it off they take the host-driven path.  Either way results stay element-wise equal to
     the oracle (planted profiles of several densities,
     a clustered profile, sparse and low-rank products, rectangular shapes)."""
