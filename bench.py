@@ -384,16 +384,55 @@ def time_batch(dev, workers=16):
     def one_by_one(mats):
         return [pluq.pluq_mod_p(a, bt.p, workspace=ws)[2] for a in mats]
 
+    def persistent():
+        """One persistent launch (largest matrices first), then the same call
+        captured in a CUDA graph and replayed on the original inputs."""
+        mats = [a.clone() for a in originals]
+        b = pluq.PersistentBatch(mats, bt.p)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        b.run()                               # warm-up
+        torch.cuda.synchronize()
+        for a, o in zip(mats, originals):
+            a.copy_(o)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_launch, ranks_launch = e0.elapsed_time(e1), b.ranks()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            b.run()
+        for a, o in zip(mats, originals):
+            a.copy_(o)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_graph, ranks_graph = e0.elapsed_time(e1), b.ranks()
+        ctas = torch.cuda.get_device_properties(dev).multi_processor_count   # ctas = 0: one per SM
+        del mats, b, graph
+        return ms_launch, ranks_launch, ms_graph, ranks_graph, ctas
+
     timed(pool)                               # warm-up (kernels, host pools)
     ms_pool, ranks_pool = timed(pool)
     ms_one, ranks_one = timed(one_by_one)
+    ms_pers, ranks_pers, ms_graph, ranks_graph, ctas = persistent()
     del originals, ws
     return {"count": len(bt.ms), "p": bt.p, "sizes": "m, n uniform in [64, 2048]",
             "rank": "floor(min(m, n) / 2), planted", "fops_total": work,
+            "persistent_launch": {"ctas": ctas, "ms": ms_pers,
+                                  "value": work / (ms_pers / 1e3) / 1e9, "unit": UNIT,
+                                  "note": "one launch, a thread block per SM, largest first"},
+            "persistent_graph_replay": {"ms": ms_graph,
+                                        "value": work / (ms_graph / 1e3) / 1e9, "unit": UNIT},
             "worker_pool": {"workers": workers, "ms": ms_pool,
                             "value": work / (ms_pool / 1e3) / 1e9, "unit": UNIT},
             "one_at_a_time": {"ms": ms_one, "value": work / (ms_one / 1e3) / 1e9, "unit": UNIT},
-            "ranks_equal_planted": ranks_pool == bt.rs and ranks_one == bt.rs}
+            "ranks_equal_planted": (ranks_pool == bt.rs and ranks_one == bt.rs and
+                                    ranks_pers == bt.rs and ranks_graph == bt.rs)}
 
 
 def other_workloads(args, dev, flush):

@@ -108,6 +108,36 @@ pluq_status pluq_mod_p_batched(uint32_t *const *h_dA, const int64_t *h_m, const 
                                int workers, void *stream);
 
 /*
+ * The same batch in ONE persistent launch (Algorithm 1, Sec. 2, for every
+ * matrix; the recursion runs on the device, no host round trip).  `ctas`
+ * thread blocks (0: one per SM) each take the next matrix from a device-side
+ * counter, in array order (put the largest first for balance), and factor it
+ * to the end on one SM.  Every argument array is DEVICE memory of length
+ * `count`: d_A[i] (m[i] x n[i], stride lda[i] >= n[i]), d_m, d_n, d_lda,
+ * output vectors d_perm_p[i] / d_perm_q[i] (device), and d_rank[i], which
+ * receives r, or a negative status for that matrix alone (EINVAL: m or n
+ * outside [0, max_m] x [0, max_n], or a null pointer or lda < n; ERANGE: an
+ * entry >= p, the matrix left untouched; ETIMEOUT: a bounded wait gave up).
+ * Every matrix gets the packed output contract of pluq_mod_p; results do not
+ * depend on ctas.  max_m, max_n <= 2048 (sixteen base-case blocks).
+ * Asynchronous on `stream`: one memset and one kernel launch, no host
+ * synchronisation, so a warmed-up call can be captured in a CUDA graph and
+ * replayed.  The d_rank values are valid once the stream reaches that point.
+ * Workspace: pluq_batched_persistent_workspace_size(max_m, max_n, ctas),
+ * 16-byte aligned; calls that share a workspace must not overlap.
+ * Host-checked errors: EINVAL (count < 0, ctas < 0, max_m / max_n out of
+ * range, null arrays), ENOTPRIME, ENOMEM (workspace), ECUDA.
+ */
+pluq_status pluq_batched_persistent_workspace_size(int64_t max_m, int64_t max_n, int ctas,
+                                                   size_t *h_bytes);
+pluq_status pluq_mod_p_batched_persistent(uint32_t *const *d_A, const int64_t *d_m,
+                                          const int64_t *d_n, const int64_t *d_lda, int64_t count,
+                                          int64_t max_m, int64_t max_n, uint32_t p,
+                                          int32_t *const *d_perm_p, int32_t *const *d_perm_q,
+                                          int64_t *d_rank, void *d_work, size_t ws_bytes, int ctas,
+                                          void *stream);
+
+/*
  * Row rank profile of A (Corollary of Lemma 2, Sec. 4): the sorted first r
  * entries of perm_p.  d_out receives r int32.  Asynchronous on `stream`.
  */

@@ -297,6 +297,7 @@ size_t mm_tc_group_workspace(const MMSpec *spec, int count, int64_t K, uint32_t 
 int tc_error_flag();
 int leaf_error_flag();        // either kind of base-case kernel gave up a wait
 int node_leaf_error_flag();   // the node kernel's base cases (part of leaf_error_flag)
+int batch_leaf_error_flag();  // the persistent batch kernel's base cases (likewise)
 
 // Tries of every abortable device-side wait (pluq_set_wait_limit): negative
 // keeps each kernel's built-in bound.  The waits a kernel runs while winding

@@ -70,7 +70,7 @@ int leaf_error_flag()
     int v = 0, z = 0;
     if (cudaMemcpyFromSymbol(&v, g_leaf_error, sizeof(int)) != cudaSuccess) return 0;
     if (v) cudaMemcpyToSymbol(g_leaf_error, &z, sizeof(int));
-    return v | node_leaf_error_flag();
+    return v | node_leaf_error_flag() | batch_leaf_error_flag();
 }
 
 }  // namespace pluq

@@ -73,6 +73,10 @@ _SIGS = {
     "pluq_modmm_tensor_noalloc": (ctypes.c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _c_i64, _c_i64,
                                                  _c_i64, _c_i64, _c_u32, ctypes.c_int, _vp]),
     "pluq_batched_workspace_size": (ctypes.c_int, [_i64p, _i64p, _c_i64, _c_u32, ctypes.c_int, _szp]),
+    "pluq_batched_persistent_workspace_size": (ctypes.c_int, [_c_i64, _c_i64, ctypes.c_int, _szp]),
+    "pluq_mod_p_batched_persistent": (ctypes.c_int, [_vp, _vp, _vp, _vp, _c_i64, _c_i64, _c_i64,
+                                                     _c_u32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                                     ctypes.c_int, _vp]),
     "pluq_mod_p_batched": (ctypes.c_int, [ctypes.POINTER(_vp), _i64p, _i64p, _i64p, _c_i64, _c_u32,
                                           ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64p, _vp,
                                           ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _vp]),
@@ -528,6 +532,87 @@ def pluq_mod_p_batched(mats, p: int, mm: str = "auto", workers: int = 8, workspa
                                      _stream(stream)), "pluq_mod_p_batched")
     return ([pps[i][:shapes[i][0]] for i in range(cnt)], [pqs[i][:shapes[i][1]] for i in range(cnt)],
             [int(ranks[i]) for i in range(cnt)])
+
+
+def pluq_batched_persistent_workspace_size(max_m: int, max_n: int, ctas: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().pluq_batched_persistent_workspace_size(int(max_m), int(max_n), int(ctas),
+                                                         ctypes.byref(out)),
+           "pluq_batched_persistent_workspace_size")
+    return int(out.value)
+
+
+class PersistentBatch:
+    """A batch for pluq_mod_p_batched_persistent: the device-side argument
+    arrays (matrices largest first, by m n min(m, n)), the output vectors and
+    the workspace, built once.  `run()` queues the call (one memset, one
+    launch) on the current stream; after a first run it can be captured in a
+    CUDA graph and replayed on new contents of the same matrices.  `ranks()`
+    gives the ranks (or negative per-matrix statuses) in the order of `mats`."""
+
+    def __init__(self, mats, p: int, ctas: int = 0, workspace=None):
+        _need_cuda(*mats)
+        for A in mats:
+            if A.dim() != 2 or (A.shape[0] > 1 and A.shape[1] > 1 and A.stride(1) != 1):
+                raise ValueError("matrices must be 2-D with contiguous rows")
+        self.mats, self.p, self.ctas = list(mats), int(p), int(ctas)
+        cnt = len(self.mats)
+        dev = self.mats[0].device if cnt else torch.device("cuda")
+        shapes = [tuple(A.shape) for A in self.mats]
+        self.pps = [torch.empty(max(m, 1), dtype=torch.int32, device=dev) for m, _ in shapes]
+        self.pqs = [torch.empty(max(n, 1), dtype=torch.int32, device=dev) for _, n in shapes]
+        self.order = sorted(range(cnt), key=lambda i: -shapes[i][0] * shapes[i][1] *
+                            min(shapes[i][0], shapes[i][1]))
+        o = self.order
+
+        def i64(vals):
+            return torch.tensor(vals, dtype=torch.int64).to(dev)
+
+        self.d_A = i64([self.mats[i].data_ptr() if self.mats[i].numel() else 0 for i in o])
+        self.d_m = i64([shapes[i][0] for i in o])
+        self.d_n = i64([shapes[i][1] for i in o])
+        self.d_lda = i64([(self.mats[i].stride(0) if shapes[i][0] > 1 else max(shapes[i][1], 1))
+                          for i in o])
+        self.d_pp = i64([self.pps[i].data_ptr() for i in o])
+        self.d_pq = i64([self.pqs[i].data_ptr() for i in o])
+        self.d_rank = torch.zeros(max(cnt, 1), dtype=torch.int64, device=dev)
+        self.max_m = max([m for m, _ in shapes], default=0)
+        self.max_n = max([n for _, n in shapes], default=0)
+        ws = pluq_batched_persistent_workspace_size(self.max_m, self.max_n, self.ctas)
+        if workspace is None or workspace.numel() < ws:
+            workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.workspace = workspace
+
+    def run(self, stream=None):
+        _check(load().pluq_mod_p_batched_persistent(
+            _ptr(self.d_A), _ptr(self.d_m), _ptr(self.d_n), _ptr(self.d_lda), len(self.mats),
+            self.max_m, self.max_n, self.p, _ptr(self.d_pp), _ptr(self.d_pq), _ptr(self.d_rank),
+            _ptr(self.workspace), self.workspace.numel(), self.ctas, _stream(stream)),
+            "pluq_mod_p_batched_persistent")
+
+    def ranks(self):
+        got = self.d_rank.cpu().tolist()
+        out = [0] * len(self.mats)
+        for pos, i in enumerate(self.order):
+            out[i] = int(got[pos])
+        return out
+
+    def perms(self):
+        return ([self.pps[i][:A.shape[0]] for i, A in enumerate(self.mats)],
+                [self.pqs[i][:A.shape[1]] for i, A in enumerate(self.mats)])
+
+
+def pluq_mod_p_batched_persistent(mats, p: int, ctas: int = 0, workspace=None, stream=None):
+    """In-place PLUQ of every matrix in `mats` (int32 CUDA tensors, rows
+    contiguous, sides <= 2048) in one persistent launch.  Returns (list of
+    perm_p, list of perm_q, list of ranks); a negative rank is that matrix's
+    status (PLUQ_ERANGE, PLUQ_EINVAL, PLUQ_ETIMEOUT)."""
+    if not mats:
+        return [], [], []
+    b = PersistentBatch(mats, p, ctas, workspace)
+    b.run(stream)
+    pps, pqs = b.perms()
+    return pps, pqs, b.ranks()
 
 
 def pluq_set_tuning(leaf: int, small_mm_macs: int):

@@ -114,6 +114,39 @@ def test_uses_reject_bad_arguments_on_the_host():
                           None, 0, None) == einval                                        # no flag
 
 
+def test_persistent_batch_rejects_bad_arguments_on_the_host():
+    """The persistent batch entry point and its workspace query check sizes,
+    the modulus, the argument arrays and the workspace before any device work
+    (the device arrays are never dereferenced here)."""
+    import ctypes
+    lib = pluq.load()
+    out = ctypes.c_size_t(0)
+    ok, einval, enotprime, enomem = 0, -1, -2, -4
+    f = lib.pluq_batched_persistent_workspace_size
+    assert f(2049, 10, 4, ctypes.byref(out)) == einval     # beyond sixteen base-case blocks
+    assert f(10, -1, 4, ctypes.byref(out)) == einval
+    assert f(10, 10, -1, ctypes.byref(out)) == einval      # ctas < 0
+    assert f(2048, 2048, 4, ctypes.byref(out)) == ok
+    big = out.value
+    assert big >= 4 * (2048 * 2048 + 1025 * 1025) * 4      # four blocks' stage and copy of I
+    assert f(100, 30, 4, ctypes.byref(out)) == ok and 0 < out.value < big
+    need = out.value
+    fake = 4096
+    run = lib.pluq_mod_p_batched_persistent
+    assert run(fake, fake, fake, fake, -1, 100, 30, 65521, fake, fake, fake, fake, need, 4,
+               None) == einval                                                 # count < 0
+    assert run(fake, fake, fake, fake, 3, 2049, 30, 65521, fake, fake, fake, fake, need, 4,
+               None) == einval                                                 # max_m
+    assert run(fake, fake, fake, fake, 3, 100, 30, 65535, fake, fake, fake, fake, need, 4,
+               None) == enotprime
+    assert run(fake, None, fake, fake, 3, 100, 30, 65521, fake, fake, fake, fake, need, 4,
+               None) == einval                                                 # no m array
+    assert run(fake, fake, fake, fake, 3, 100, 30, 65521, fake, fake, fake, fake, need - 1, 4,
+               None) == enomem
+    assert run(fake, fake, fake, fake, 0, 100, 30, 65521, fake, fake, fake, None, 0, 4,
+               None) == ok                                                     # empty batch
+
+
 def test_autotune_cache_lookup_on_the_host(tmp_path):
     """Workload classes round sizes up to powers of two and separate limb
     counts and dense / deficient inputs; apply() sets the library's knobs
