@@ -53,19 +53,25 @@ def parse():
                     help="skip the other workloads (256^2, 4096^2, 8192x32768, batch)")
     ap.add_argument("--mm", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["pluq", "planted", "gemm", "leaf", "trsm", "perm"],
+    ap.add_argument("--profile", choices=["pluq", "planted", "gemm", "leaf", "trsm", "perm", "batch"],
                     default=None,
                     help="untimed: one warm-up and one decomposition of the workload (pluq) or "
                          "of a planted --shape M,N matrix of --rank mod --p (planted), one "
                          "modular product of --shape M,N,K (gemm), one base-case call on a "
                          "uniform --shape M,N block (leaf), the left and right triangular "
                          "solves with an r x r triangle and N right-hand sides, --shape r,N "
-                         "(trsm), or PermR and PermC of an --shape M,N matrix by random "
-                         "permutations (perm), each twice, for external profilers")
+                         "(trsm), PermR and PermC of an --shape M,N matrix by random "
+                         "permutations (perm), or a planted uneven batch of --shape "
+                         "count,largest-side matrices in one persistent launch (batch), each "
+                         "twice, for external profilers")
     ap.add_argument("--shape", default="8192,8192,2048",
-                    help="sizes for --profile gemm / leaf / trsm / perm")
+                    help="sizes for --profile gemm / leaf / trsm / perm / batch")
     ap.add_argument("--p", type=int, default=65521, help="modulus for --profile gemm / planted")
     ap.add_argument("--rank", type=int, default=None, help="rank for --profile planted")
+    ap.add_argument("--node-levels", type=int, default=None,
+                    help="node kernel levels for --profile pluq / planted (default: tuned)")
+    ap.add_argument("--node-ctas", type=int, default=None,
+                    help="node kernel thread blocks for --profile pluq / planted (default: tuned)")
     return ap.parse_args()
 
 
@@ -98,6 +104,20 @@ def run_profile_target(args):
         for _ in range(2):
             pluq.pluq_perm_rows(X, pr, workspace=ws)
             pluq.pluq_perm_cols(X, pc, workspace=ws)
+    elif args.profile == "batch":
+        # --shape count,largest side: an uneven planted batch in one persistent launch
+        count, hi = (int(x) for x in args.shape.split(",")[:2])
+        bt = W.batch_2000(count=count, hi=hi)
+        mats = [W.planted_device(m, n, r, bt.p, sd, "cuda")[0]
+                for m, n, r, sd in zip(bt.ms, bt.ns, bt.rs, bt.seeds)]
+        originals = [a.clone() for a in mats]
+        b = pluq.PersistentBatch(mats, bt.p)
+        for _ in range(2):
+            for a, o in zip(mats, originals):
+                a.copy_(o)
+            b.run()
+        torch.cuda.synchronize()
+        assert b.ranks() == bt.rs
     elif args.profile == "gemm":
         M, N, K = (int(x) for x in args.shape.split(","))
         p = args.p
@@ -122,6 +142,10 @@ def run_profile_target(args):
         from paper_1301_4438_gb300 import autotune
         autotune.apply(cfg.m, cfg.n, cfg.p, deficient=cfg.kind == "planted",
                        cache=os.path.join(ROOT, "_build_tuning.json"))
+        if args.node_levels is not None:
+            pluq.pluq_set_node_kernel(args.node_levels)
+        if args.node_ctas is not None:
+            pluq.pluq_set_node_cluster(args.node_ctas)
         for it in range(2):
             A = A0.clone()
             torch.cuda.synchronize()
@@ -216,7 +240,8 @@ def cpu_oracle_rate(target_s: float = 12.0, p: int = 65521):
 # ---------------------------------------------------------- roofline input --
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mm_tc.cu", "common.cuh", "leaf.cu", "perm.cu"):
+    for f in ("mm_tc.cu", "common.cuh", "leaf_impl.cuh", "leaf.cu", "node_impl.cuh", "node.cu",
+              "batch.cu", "perm.cu"):
         with open(os.path.join(ROOT, "paper_1301_4438_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -425,7 +450,16 @@ def time_batch(dev, workers=16):
             "rank": "floor(min(m, n) / 2), planted", "fops_total": work,
             "persistent_launch": {"ctas": ctas, "ms": ms_pers,
                                   "value": work / (ms_pers / 1e3) / 1e9, "unit": UNIT,
-                                  "note": "one launch, a thread block per SM, largest first"},
+                                  "note": "one launch, a thread block per SM, largest first",
+                                  "roofline": {"kernel": "batch_kernel", "bound": "alu",
+                                               "achieved": work / (ms_pers / 1e3) / 1e9,
+                                               "peak": alu_field_peak(), "unit": "Gfop/s",
+                                               "frac": work / (ms_pers / 1e3) / 1e9 / alu_field_peak(),
+                                               "peak_source": "derived: 152 SMs x 128 lanes x max SM "
+                                                              "clock, at 5 lane instructions per "
+                                                              "field operation",
+                                               "work": "fops(m, n, r) summed over the batch (the "
+                                                       "field operations of each elimination)"}},
             "persistent_graph_replay": {"ms": ms_graph,
                                         "value": work / (ms_graph / 1e3) / 1e9, "unit": UNIT},
             "worker_pool": {"workers": workers, "ms": ms_pool,

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(LT, 1) batch_kernel(const __grid_constant__ Ba
     NodeArgs na{};
     na.F = a.F;
     na.stage = a.stage + (int64_t)blockIdx.x * a.slice_words;
+    na.stage_words = a.stage_words;
     na.icopy = na.stage + a.stage_words;
     na.wait_limit = a.wait_limit;
     na.left_looking = a.left_looking;
@@ -110,7 +111,9 @@ constexpr int64_t round_words(int64_t w) { return (w + 63) & ~(int64_t)63; }
 
 void slice_words(int64_t max_m, int64_t max_n, int64_t &stage, int64_t &icopy, int64_t &slice)
 {
-    stage = round_words(max_m * max_n);
+    // a node's permutations stage at most three block heights of rows, each
+    // padded by up to 6 words for 16-byte accesses
+    stage = round_words(max_m * max_n + 24 * max_m + 64);
     icopy = round_words((max_m / 2 + 1) * (max_n / 2 + 1));
     slice = stage + icopy;
 }

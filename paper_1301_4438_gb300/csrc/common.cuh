@@ -386,11 +386,12 @@ pluq_status launch_leaf(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
 
 // Algorithm 1 on a node of at most 4 LEAF_MAX x 4 LEAF_MAX in one thread
 // block: its blocks are base cases, or (above 2 LEAF_MAX) nodes whose blocks
-// are; same outputs and host words as launch_leaf.  stage holds m * n words,
-// icopy ceil(m/2) * ceil(n/2).
+// are; same outputs and host words as launch_leaf.  stage holds stage_words
+// >= m * n words, icopy ceil(m/2) * ceil(n/2).
 pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F, int32_t *perm_p,
                         int32_t *perm_q, int32_t *info, cudaStream_t st, volatile int32_t *host_info,
-                        int32_t seq, bool try_generic, uint32_t *stage, uint32_t *icopy);
+                        int32_t seq, bool try_generic, uint32_t *stage, int64_t stage_words,
+                        uint32_t *icopy);
 
 // Process-wide tuning (pluq_set_tuning): leaf size of the recursion, and the
 // number of multiply-adds below which a product goes to the CUDA-core kernel

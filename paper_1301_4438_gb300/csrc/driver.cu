@@ -505,7 +505,7 @@ pluq_status rec(Ctx &c, uint32_t *A, int64_t m, int64_t n, int64_t lda, int32_t 
     if (eager && node_levels > 0 && m <= node_side && n <= node_side) {
         const int32_t seq = ++c.hw->seq;
         PLUQ_TRY(launch_node(A, m, n, lda, c.F, pp, pq, c.d_rank + 4, c.st, c.hw->d, seq, false,
-                             c.gather, c.icopy));
+                             c.gather, (int64_t)c.gather_elems, c.icopy));
         PLUQ_TRY(wait_words(c.hw, seq, c.st));
         const int32_t r = c.hw->h[1];
         ++c.leaves;

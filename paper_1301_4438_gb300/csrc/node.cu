@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(LT, 1) node_kernel(const __grid_constant__ Nod
 
 pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F, int32_t *perm_p,
                         int32_t *perm_q, int32_t *info, cudaStream_t st, volatile int32_t *host_info,
-                        int32_t seq, bool try_generic, uint32_t *stage, uint32_t *icopy)
+                        int32_t seq, bool try_generic, uint32_t *stage, int64_t stage_words,
+                        uint32_t *icopy)
 {
     if (m <= 0 || n <= 0 || m > NMAX || n > NMAX) return PLUQ_EINVAL;
     NodeArgs a{};
@@ -50,6 +51,7 @@ pluq_status launch_node(uint32_t *A, int64_t m, int64_t n, int64_t lda, Field F,
     a.host_info = host_info;
     a.seq = seq;
     a.stage = stage;
+    a.stage_words = stage_words;
     a.icopy = icopy;
     a.wait_limit = wait_limit_or(STEP_WAIT_LIMIT);
     a.try_generic = try_generic ? 1 : 0;

@@ -151,25 +151,103 @@ struct NdPerm {
     const int32_t *rmap, *cmap;
 };
 
-// The permutations of a phase, on disjoint blocks, through disjoint slices of
-// the global area `stage`: every block is gathered, then (after one barrier)
-// copied back.  Ends with its own barrier; none if no block moves.
-template <int NC>
-__device__ void nd_perms(const NdPerm *ops, int count, int64_t ld, uint32_t *stage, const Grp<NC> &g)
+// Word phase of an address within its 16-byte line.
+__device__ __forceinline__ int word_phase(const void *p) { return (int)(((uintptr_t)p >> 2) & 3); }
+
+// One warp copies `cols` words from src to dst, which share their phase:
+// scalar head up to the 16-byte boundary, 16-byte body (two loads in flight
+// per lane), scalar tail.
+__device__ __forceinline__ void warp_row_copy16(uint32_t *dst, const uint32_t *src, int cols, int lane)
 {
-    bool any = false;
+    const int head = min(cols, (4 - word_phase(src)) & 3);
+    if (lane < head) dst[lane] = src[lane];
+    const int nv = (cols - head) >> 2;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src + head);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst + head);
+    int v = lane;
+    for (; v + 32 < nv; v += 64) {
+        const uint4 a = s4[v], b = s4[v + 32];
+        d4[v] = a;
+        d4[v + 32] = b;
+    }
+    if (v < nv) d4[v] = s4[v];
+    const int t = head + 4 * nv + lane;
+    if (t < cols) dst[t] = src[t];
+}
+
+// Blocks at least this wide move a row per warp (16-byte accesses where the
+// row stride allows); narrower ones element by element over all threads.
+constexpr int ND_ROW_COLS = 64;
+
+// Stage layout of one op: row mode keeps every staged row at the phase of
+// the block's rows (pitch a multiple of 4 words, 16-byte aligned start) so
+// that both copies can use 16-byte accesses.
+struct NdLayout {
+    bool rowwise;
+    int ph, pitch;
+};
+
+__device__ __forceinline__ NdLayout nd_layout(const NdPerm &q, bool vec)
+{
+    NdLayout L;
+    L.rowwise = q.cols >= ND_ROW_COLS;
+    L.ph = L.rowwise && vec ? word_phase(q.X) : 0;
+    L.pitch = L.rowwise && vec ? ((q.cols + L.ph + 3) & ~3) : q.cols;
+    return L;
+}
+
+// The permutations of a phase, on disjoint blocks, through disjoint slices of
+// the global area `stage` (stage_words long): every block is gathered, then
+// (after one barrier) copied back.  Wide blocks go a row per warp, CTAs taking
+// row ranges: a row permutation moves whole rows with 16-byte accesses (when
+// the row stride is a multiple of 4 words and the padded layout fits in the
+// stage), a column permutation gathers each row's words through the map.
+// Ends with its own barrier; none if no block moves.
+template <int NC>
+__device__ void nd_perms(const NdPerm *ops, int count, int64_t ld, uint32_t *stage,
+                         int64_t stage_words, const Grp<NC> &g)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool any = false, vec = (ld & 3) == 0 && (((uintptr_t)stage) & 15) == 0;
+    if (vec) {
+        int64_t need = 0;
+        for (int o = 0; o < count; ++o) {
+            const NdPerm &q = ops[o];
+            if (q.rows <= 0 || q.cols <= 0 || (!q.rmap && !q.cmap)) continue;
+            const NdLayout L = nd_layout(q, true);
+            need = ((need + 3) & ~(int64_t)3) + (int64_t)q.rows * L.pitch;
+        }
+        vec = need <= stage_words;
+    }
     int64_t off = 0;
     for (int o = 0; o < count; ++o) {
         const NdPerm &q = ops[o];
         if (q.rows <= 0 || q.cols <= 0 || (!q.rmap && !q.cmap)) continue;
         any = true;
-        int lo, hi;
-        g.range(q.rows * q.cols, lo, hi);
-        for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
-            const int i = e / q.cols, j = e - (e / q.cols) * q.cols;
-            stage[off + e] = q.X[(int64_t)(q.rmap ? q.rmap[i] : i) * ld + (q.cmap ? q.cmap[j] : j)];
+        const NdLayout L = nd_layout(q, vec);
+        if (vec) off = (off + 3) & ~(int64_t)3;
+        if (L.rowwise) {
+            int lo, hi;
+            g.range(q.rows, lo, hi);
+            for (int i = lo + warp; i < hi; i += NW) {
+                const uint32_t *src = q.X + (int64_t)(q.rmap ? q.rmap[i] : i) * ld;
+                uint32_t *dst = stage + off + (int64_t)i * L.pitch + L.ph;
+                if (q.cmap)
+                    for (int j = lane; j < q.cols; j += 32) dst[j] = src[q.cmap[j]];
+                else if (vec)
+                    warp_row_copy16(dst, src, q.cols, lane);
+                else
+                    for (int j = lane; j < q.cols; j += 32) dst[j] = src[j];
+            }
+        } else {
+            int lo, hi;
+            g.range(q.rows * q.cols, lo, hi);
+            for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
+                const int i = e / q.cols, j = e - (e / q.cols) * q.cols;
+                stage[off + e] = q.X[(int64_t)(q.rmap ? q.rmap[i] : i) * ld + (q.cmap ? q.cmap[j] : j)];
+            }
         }
-        off += (int64_t)q.rows * q.cols;
+        off += (int64_t)q.rows * L.pitch;
     }
     if (!any) return;
     g.sync();
@@ -177,23 +255,46 @@ __device__ void nd_perms(const NdPerm *ops, int count, int64_t ld, uint32_t *sta
     for (int o = 0; o < count; ++o) {
         const NdPerm &q = ops[o];
         if (q.rows <= 0 || q.cols <= 0 || (!q.rmap && !q.cmap)) continue;
-        int lo, hi;
-        g.range(q.rows * q.cols, lo, hi);
-        for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
-            const int i = e / q.cols, j = e - (e / q.cols) * q.cols;
-            q.X[(int64_t)i * ld + j] = stage[off + e];
+        const NdLayout L = nd_layout(q, vec);
+        if (vec) off = (off + 3) & ~(int64_t)3;
+        if (L.rowwise) {
+            int lo, hi;
+            g.range(q.rows, lo, hi);
+            for (int i = lo + warp; i < hi; i += NW) {
+                const uint32_t *src = stage + off + (int64_t)i * L.pitch + L.ph;
+                uint32_t *dst = q.X + (int64_t)i * ld;
+                if (vec)
+                    warp_row_copy16(dst, src, q.cols, lane);
+                else
+                    for (int j = lane; j < q.cols; j += 32) dst[j] = src[j];
+            }
+        } else {
+            int lo, hi;
+            g.range(q.rows * q.cols, lo, hi);
+            for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
+                const int i = e / q.cols, j = e - (e / q.cols) * q.cols;
+                q.X[(int64_t)i * ld + j] = stage[off + e];
+            }
         }
-        off += (int64_t)q.rows * q.cols;
+        off += (int64_t)q.rows * L.pitch;
     }
     g.sync();
 }
 
-// dst (rows x cols) <- src, this CTA's share of the elements
+// dst (rows x cols) <- src, this CTA's share of the rows (a row per warp) or,
+// for narrow blocks, of the elements
 template <int NC>
 __device__ void nd_copy(uint32_t *dst, int64_t ldd, const uint32_t *src, int64_t lds, int rows,
                         int cols, const Grp<NC> &g)
 {
     int lo, hi;
+    if (cols >= ND_ROW_COLS) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        g.range(rows, lo, hi);
+        for (int i = lo + warp; i < hi; i += NW)
+            for (int j = lane; j < cols; j += 32) dst[(int64_t)i * ldd + j] = src[(int64_t)i * lds + j];
+        return;
+    }
     g.range(rows * cols, lo, hi);
     for (int e = lo + (int)threadIdx.x; e < hi; e += LT) {
         const int i = e / cols, j = e - (e / cols) * cols;
@@ -267,6 +368,59 @@ __device__ void nd_trsm_right(const uint32_t *U, int64_t ldu, uint32_t *B, int64
     }
 }
 
+// C (M x N) <- C - A B for shallow products (K < MM_TILED_K): a row of C per
+// warp.  Where the rows of C and B share their 16-byte phase (and the strides
+// are multiples of 4 words) each lane takes four adjacent columns with 16-byte
+// accesses, the columns before the first and after the last 16-byte boundary
+// one per lane; otherwise every column is one per lane.  The K entries of A's
+// row are read by the whole warp at once.  Each output one delayed reduction.
+template <bool SMALLP>
+__device__ void nd_mm_sub_shallow(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t lda,
+                                  const uint32_t *B, int64_t ldb, int M, int N, int K, const Field &F)
+{
+    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = N >= 8 && ((ldc | ldb) & 3) == 0 && word_phase(C) == word_phase(B);
+    const int head = vec ? min(N, (4 - word_phase(C)) & 3) : N;   // one per lane, before the body
+    const int nv = vec ? (N - head) >> 2 : 0;                       // 16-byte groups
+    const int tail0 = head + 4 * nv;                                // one per lane, after the body
+    const int ns = head + (N - tail0);
+    for (int i = warp; i < M; i += NW) {
+        uint32_t *c = C + (int64_t)i * ldc;
+        const uint32_t *a = A + (int64_t)i * lda;
+        uint32_t av[MM_TILED_K];
+#pragma unroll
+        for (int l = 0; l < MM_TILED_K; ++l) av[l] = l < K ? a[l] : 0u;
+        for (int v = lane; v < nv; v += 32) {
+            const int j = head + 4 * v;
+            LAcc<SMALLP> acc[4];
+#pragma unroll
+            for (int l = 0; l < MM_TILED_K; ++l)
+                if (l < K) {
+                    const uint4 y = *reinterpret_cast<const uint4 *>(B + (int64_t)l * ldb + j);
+                    acc[0].add(av[l], y.x);
+                    acc[1].add(av[l], y.y);
+                    acc[2].add(av[l], y.z);
+                    acc[3].add(av[l], y.w);
+                }
+            uint4 x = *reinterpret_cast<const uint4 *>(c + j);
+            x.x = sub_mod(x.x, acc[0].value(F, w16), F.p);
+            x.y = sub_mod(x.y, acc[1].value(F, w16), F.p);
+            x.z = sub_mod(x.z, acc[2].value(F, w16), F.p);
+            x.w = sub_mod(x.w, acc[3].value(F, w16), F.p);
+            *reinterpret_cast<uint4 *>(c + j) = x;
+        }
+        for (int t = lane; t < ns; t += 32) {
+            const int j = t < head ? t : tail0 + (t - head);
+            LAcc<SMALLP> acc;
+#pragma unroll
+            for (int l = 0; l < MM_TILED_K; ++l)
+                if (l < K) acc.add(av[l], B[(int64_t)l * ldb + j]);
+            c[j] = sub_mod(c[j], acc.value(F, w16), F.p);
+        }
+    }
+}
+
 // C (M x N) <- C - A B, A M x K, B K x N, this CTA's share of the rows: each
 // output one delayed reduction, or (K >= MM_TILED_K) through nd_mm_sub_tiled;
 // ends with a block barrier where it ran
@@ -285,14 +439,7 @@ __device__ void nd_mm_sub(uint32_t *C, int64_t ldc, const uint32_t *A, int64_t l
         nd_mm_sub_tiled<SMALLP>(C, ldc, A, lda, B, ldb, M, N, K, F, sm);
         return;
     }
-    const uint32_t w16 = (uint32_t)((1ull << 16) % F.p);
-    const int tot = M * N;
-    for (int e = threadIdx.x; e < tot; e += LT) {
-        const int i = e / N, j = e - (e / N) * N;
-        LAcc<SMALLP> acc;
-        for (int l = 0; l < K; ++l) acc.add(A[(int64_t)i * lda + l], B[(int64_t)l * ldb + j]);
-        C[(int64_t)i * ldc + j] = sub_mod(C[(int64_t)i * ldc + j], acc.value(F, w16), F.p);
-    }
+    nd_mm_sub_shallow<SMALLP>(C, ldc, A, lda, B, ldb, M, N, K, F);
     __syncthreads();
 }
 
@@ -327,10 +474,35 @@ __device__ bool nd_any_nonzero(const uint32_t *X, int64_t ld, int rows, int cols
                                const Grp<NC> &g)
 {
     int lo, hi;
-    g.range(rows * cols, lo, hi);
     bool nz = false;
-    for (int e = lo + (int)threadIdx.x; e < hi && !nz; e += LT)
-        nz = X[(int64_t)(e / cols) * ld + (e - (e / cols) * cols)] != 0;
+    if (cols >= ND_ROW_COLS) {
+        // a row per warp, 16-byte loads where the row stride allows
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        g.range(rows, lo, hi);
+        for (int i = lo + warp; i < hi && !nz; i += NW) {
+            const uint32_t *row = X + (int64_t)i * ld;
+            uint32_t acc = 0;
+            if ((ld & 3) == 0) {
+                const int head = min(cols, (4 - word_phase(row)) & 3);
+                if (lane < head) acc |= row[lane];
+                const int nv = (cols - head) >> 2;
+                const uint4 *r4 = reinterpret_cast<const uint4 *>(row + head);
+                for (int v = lane; v < nv; v += 32) {
+                    const uint4 x = r4[v];
+                    acc |= x.x | x.y | x.z | x.w;
+                }
+                const int t = head + 4 * nv + lane;
+                if (t < cols) acc |= row[t];
+            } else {
+                for (int j = lane; j < cols; j += 32) acc |= row[j];
+            }
+            nz = __any_sync(0xffffffffu, acc != 0);
+        }
+    } else {
+        g.range(rows * cols, lo, hi);
+        for (int e = lo + (int)threadIdx.x; e < hi && !nz; e += LT)
+            nz = X[(int64_t)(e / cols) * ld + (e - (e / cols) * cols)] != 0;
+    }
     const bool mine = __syncthreads_or(nz);
     if constexpr (NC == 1) {
         return mine;
@@ -367,6 +539,7 @@ struct NodeArgs {
     volatile int32_t *host_info;
     int32_t seq;
     uint32_t *stage;           // at least m * n words
+    int64_t stage_words;       // its length (a padded 16-byte layout is used when it fits)
     uint32_t *icopy;           // at least (m/2 + 1) * (n/2 + 1) words
     uint32_t wait_limit;
     int try_generic, left_looking;
@@ -474,7 +647,7 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     // [B1;B2] <- P1^T A2 ; [C1 C2] <- A3 Q1^T
     {
         const NdPerm ops[2] = {{at(0, h), k, n - h, P1, nullptr}, {at(k, 0), m - k, h, nullptr, Q1}};
-        nd_perms<NC>(ops, 2, lda, a.stage, g);
+        nd_perms<NC>(ops, 2, lda, a.stage, a.stage_words, g);
     }
     // D <- L1^{-1} B1 ; E <- C1 U1^{-1} ; [F;H] <- [B2;A4] - [M1;E] D ; G <- C2 - E V1
     nd_trsm_left<SMALLP, NC>(A, lda, at(0, h), lda, r1, n - h, F, S.W, g);
@@ -503,7 +676,7 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
                                {at(r1, 0), k - r1, r1, P2, nullptr},
                                {at(0, h), r1, n - h, nullptr, Q2},
                                {at(0, r1), r1, h - r1, nullptr, Q3}};
-        nd_perms<NC>(ops, 5, lda, a.stage, g);
+        nd_perms<NC>(ops, 5, lda, a.stage, a.stage_words, g);
     }
     // [I;K] <- [H1;H3] U2^{-1} ; keep I ; [J N] <- L3^{-1} [I H2]
     nd_trsm_right<SMALLP, NC>(at(r1, h), lda, at(k, h), lda, m - k, r2, F, node_dinv<LEVEL>(NS), S.W, g);
@@ -538,7 +711,7 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     {
         const NdPerm ops[2] = {{at(k + r3, 0), m - k - r3, h + r2, P4, nullptr},
                                {at(0, h + r2), k + r3, n - h - r2, nullptr, Q4}};
-        nd_perms<NC>(ops, 2, lda, a.stage, g);
+        nd_perms<NC>(ops, 2, lda, a.stage, a.stage_words, g);
     }
     // P = Diag(P1 diag(I,P2), P3 diag(I,P4)) S, Q = T Diag(diag(I,Q3) Q1, diag(I,Q4) Q2),
     // and the row map of S / column map of T (every CTA, into its own maps)
@@ -580,7 +753,7 @@ __device__ __noinline__ void node_step(LeafShared &S, NodeShared &NS, const Node
     // A <- S^T A T^T
     {
         const NdPerm op{A, m, n, s_ident ? nullptr : N.smap, t_ident ? nullptr : N.tmap};
-        nd_perms<NC>(&op, 1, lda, a.stage, g);
+        nd_perms<NC>(&op, 1, lda, a.stage, a.stage_words, g);
     }
     int pid = s_ident, qid = t_ident;
     for (int c = 0; c < 4; ++c) {
