@@ -582,15 +582,20 @@ class PersistentBatch:
         if workspace is None or workspace.numel() < ws:
             workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
         self.workspace = workspace
+        self._stream = None
 
     def run(self, stream=None):
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
         _check(load().pluq_mod_p_batched_persistent(
             _ptr(self.d_A), _ptr(self.d_m), _ptr(self.d_n), _ptr(self.d_lda), len(self.mats),
             self.max_m, self.max_n, self.p, _ptr(self.d_pp), _ptr(self.d_pq), _ptr(self.d_rank),
-            _ptr(self.workspace), self.workspace.numel(), self.ctas, _stream(stream)),
+            _ptr(self.workspace), self.workspace.numel(), self.ctas, _stream(self._stream)),
             "pluq_mod_p_batched_persistent")
 
     def ranks(self):
+        """Waits for the stream of the last run(), then reads the ranks."""
+        if self._stream is not None:
+            self._stream.synchronize()
         got = self.d_rank.cpu().tolist()
         out = [0] * len(self.mats)
         for pos, i in enumerate(self.order):
