@@ -308,6 +308,23 @@ def whole_job_rate(world: int, steps: int, work_per_step: float, total_ms: float
     return world * steps * work_per_step / (total_ms / 1e3) / 1e9
 
 
+def batch_shard(work, rank: int, world: int):
+    """The matrices of an uneven batch that `rank` of `world` factors: the batch
+    shards by matrix with no data exchange (its matrices are independent).
+    Longest processing time first over the per-matrix work, ties by index, so
+    every rank computes the same assignment; returns this rank's indices,
+    largest first."""
+    order = sorted(range(len(work)), key=lambda i: (-work[i], i))
+    loads = [0.0] * world
+    mine = []
+    for i in order:
+        r = min(range(world), key=lambda k: (loads[k], k))
+        loads[r] += work[i]
+        if r == rank:
+            mine.append(i)
+    return mine
+
+
 def load_workload(cfg, dev):
     """(device int32 copy of the workload matrix, host numpy copy)."""
     import torch
@@ -375,14 +392,57 @@ def time_single(cfg, mm, steps, warmup, dev, flush):
     return out
 
 
+def time_batch_sharded(dev, bt, world: int, rank: int):
+    """The uneven batch over `world` ranks (one GPU each): every rank factors
+    its shard (batch_shard) in one persistent launch; the job's time is the
+    slowest rank's, its rate the whole batch's work over that time (strong
+    scaling: the batch is fixed)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1301_4438_gb300 import pluq, workloads as W
+    works = [fops(m, n, r) for m, n, r in zip(bt.ms, bt.ns, bt.rs)]
+    idx = batch_shard(works, rank, world)
+    originals = [W.planted_device(bt.ms[i], bt.ns[i], bt.rs[i], bt.p, bt.seeds[i], str(dev))[0]
+                 for i in idx]
+    mats = [a.clone() for a in originals]
+    b = pluq.PersistentBatch(mats, bt.p)
+    stream = torch.cuda.current_stream(dev)
+    b.run()                                   # warm-up
+    torch.cuda.synchronize()
+    for a, o in zip(mats, originals):
+        a.copy_(o)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    ok = b.ranks() == [bt.rs[i] for i in idx]
+    bad = max_over_ranks(0.0 if ok else 1.0, world)
+    work = sum(works)
+    return {"count": len(bt.ms), "p": bt.p, "sizes": "m, n uniform in [64, 2048]",
+            "rank": "floor(min(m, n) / 2), planted", "fops_total": work,
+            "persistent_launch": {"ranks": world, "ms": ms, "value": work / (ms / 1e3) / 1e9,
+                                  "unit": UNIT, "scaling": "strong",
+                                  "note": "sharded by matrix (longest first), one persistent "
+                                          "launch per rank, slowest rank's time"},
+            "ranks_equal_planted": bad == 0.0}
+
+
 def time_batch(dev, workers=16):
     """The 2000-matrix uneven batch (m, n uniform in [64, 2048], planted rank
     floor(min(m, n) / 2), p = 65521): the worker-pool entry point against one
     decomposition at a time, each over the whole batch after one warm-up pass
-    on a copy."""
+    on a copy.  Over several ranks, the sharded persistent form alone."""
     import torch
     from paper_1301_4438_gb300 import pluq, workloads as W
     bt = W.batch_2000()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        return time_batch_sharded(dev, bt, world, int(os.environ.get("RANK", "0")))
     originals = [W.planted_device(m, n, r, bt.p, sd, str(dev))[0]
                  for m, n, r, sd in zip(bt.ms, bt.ns, bt.rs, bt.seeds)]
     work = sum(fops(m, n, r) for m, n, r in zip(bt.ms, bt.ns, bt.rs))

@@ -3,7 +3,8 @@
 On the GPU each rank runs an independent replica of the decomposition (the
 path has no data exchange); the ranks meet only to take the slowest rank's
 time, and the whole-job rate counts every rank's work over that time.  The
-reference arm runs on rank 0 alone.
+uneven batch instead shards by matrix, every rank computing the same
+assignment.  The reference arm runs on rank 0 alone.
 """
 import os
 import socket
@@ -67,3 +68,61 @@ def test_reference_arm_runs_on_rank_zero_only():
                          text=True, timeout=300)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == ""
+
+
+def _batch_works():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1301_4438_gb300 import workloads as W
+    bt = W.batch_2000()
+    return bench, [bench.fops(m, n, r) for m, n, r in zip(bt.ms, bt.ns, bt.rs)]
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_batch_shards_cover_the_batch_once_and_balance(world):
+    """Over several GPUs the uneven batch shards by matrix (no data exchange):
+    the shards partition the 2000 matrices, and the longest-first assignment
+    keeps every rank's work within one matrix of the mean."""
+    bench, works = _batch_works()
+    shards = [bench.batch_shard(works, r, world) for r in range(world)]
+    flat = sorted(i for s in shards for i in s)
+    assert flat == list(range(len(works)))
+    loads = [sum(works[i] for i in s) for s in shards]
+    assert max(loads) - min(loads) <= max(works)
+    assert max(loads) <= sum(works) / world + max(works)
+    for s in shards:   # each shard is handed out largest first
+        assert [works[i] for i in s] == sorted((works[i] for i in s), reverse=True)
+
+
+def _shard_rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    bench, works = _batch_works()
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    mine = bench.batch_shard(works, rank, world)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, mine)
+    slowest = bench.max_over_ranks(sum(works[i] for i in mine), world)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, gathered, slowest))
+
+
+def test_batch_shards_agree_across_gloo_ranks():
+    """Each rank computes its own shard; gathered over two gloo ranks, the
+    shards partition the batch and the slowest rank carries the larger load."""
+    bench, works = _batch_works()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, g0, s0), (_, g1, s1) = res
+    assert g0 == g1
+    assert sorted(g0[0] + g0[1]) == list(range(len(works)))
+    assert s0 == s1 == max(sum(works[i] for i in g0[0]), sum(works[i] for i in g0[1]))
