@@ -114,6 +114,106 @@ def test_uses_reject_bad_arguments_on_the_host():
                           None, 0, None) == einval                                        # no flag
 
 
+def test_core_entry_points_reject_bad_arguments_on_the_host():
+    """The decomposition, its batched form, the read-outs and the kernel-level
+    calls check sizes, strides, pointers, the product form and the modulus
+    before any device work (the device pointers below are never
+    dereferenced), and report the statuses the header documents."""
+    import ctypes
+    lib = pluq.load()
+    ok, einval, enotprime, enomem = 0, -1, -2, -4
+    fake = 4096
+    rank = ctypes.c_int64(-1)
+    out = ctypes.c_size_t(0)
+    # pluq_workspace_size / pluq_mod_p (Algorithm 1)
+    assert lib.pluq_workspace_size(-1, 4, 65521, ctypes.byref(out)) == einval
+    assert lib.pluq_workspace_size(4, 4, 65521, None) == einval
+    assert lib.pluq_workspace_size(4, 4, 1, ctypes.byref(out)) == enotprime
+    assert lib.pluq_workspace_size(4, 4, 2147483648 - 1, ctypes.byref(out)) == ok
+    need = out.value
+    mod_p = lib.pluq_mod_p
+    assert mod_p(fake, 4, 4, 4, 65521, fake, fake, None, fake, need, 0, None) == einval   # no rank
+    assert mod_p(fake, -1, 4, 4, 65521, fake, fake, ctypes.byref(rank), fake, need, 0, None) == einval
+    assert mod_p(fake, 4, 4, 3, 65521, fake, fake, ctypes.byref(rank), fake, need, 0, None) == einval
+    assert mod_p(None, 4, 4, 4, 65521, fake, fake, ctypes.byref(rank), fake, need, 0, None) == einval
+    assert mod_p(fake, 4, 4, 4, 65521, None, fake, ctypes.byref(rank), fake, need, 0, None) == einval
+    assert mod_p(fake, 4, 4, 4, 65521, fake, fake, ctypes.byref(rank), fake, need, 3, None) == einval
+    assert mod_p(fake, 4, 4, 4, 65535, fake, fake, ctypes.byref(rank), fake, need, 0, None) == enotprime
+    assert lib.pluq_workspace_size(4, 4, 65521, ctypes.byref(out)) == ok
+    assert mod_p(fake, 4, 4, 4, 65521, fake, fake, ctypes.byref(rank), fake, out.value - 1, 0,
+                 None) == enomem
+    assert mod_p(fake, 4, 4, 4, 65521, fake, fake, ctypes.byref(rank), None, out.value, 0,
+                 None) == enomem
+    # pluq_batched_workspace_size / pluq_mod_p_batched
+    I64 = ctypes.c_int64 * 2
+    ms, ns = I64(3, 5), I64(4, 2)
+    assert lib.pluq_batched_workspace_size(ms, ns, -1, 65521, 2, ctypes.byref(out)) == einval
+    assert lib.pluq_batched_workspace_size(ms, ns, 2, 65521, 0, ctypes.byref(out)) == einval
+    assert lib.pluq_batched_workspace_size(ms, ns, 2, 9, 2, ctypes.byref(out)) == enotprime
+    assert lib.pluq_batched_workspace_size(I64(3, -5), ns, 2, 65521, 2, ctypes.byref(out)) == einval
+    assert lib.pluq_batched_workspace_size(ms, ns, 2, 65521, 2, ctypes.byref(out)) == ok
+    VP = ctypes.c_void_p * 2
+    ptrs = VP(fake, fake)
+    ranks = I64()
+    batched = lib.pluq_mod_p_batched
+    assert batched(ptrs, ms, ns, I64(4, 2), 2, 65521, ptrs, ptrs, ranks, fake, out.value, 0, 0,
+                   None) == einval                                                # no workers
+    assert batched(ptrs, ms, ns, I64(4, 1), 2, 65521, ptrs, ptrs, ranks, fake, out.value, 0, 2,
+                   None) == einval                                                # lda < n
+    assert batched(ptrs, ms, ns, I64(4, 2), 2, 65521, ptrs, ptrs, ranks, fake, out.value - 1, 0,
+                   2, None) == enomem
+    assert batched(ptrs, ms, ns, I64(4, 2), 0, 65521, ptrs, ptrs, ranks, None, 0, 0, 2,
+                   None) == ok                                                    # empty batch
+    # read-outs (Corollaries of Lemma 2, Sec. 4; Sec. 3)
+    assert lib.row_rank_profile(fake, 3, 4, fake, None) == einval                 # r > m
+    assert lib.col_rank_profile(fake, 3, -1, fake, None) == einval
+    assert lib.rank_profile_matrix(fake, fake, 3, 5, 4, fake, fake, None) == einval
+    assert lib.pluq_extract_L(fake, 4, 4, 4, 5, fake, 5, None) == einval         # r > n
+    assert lib.pluq_extract_L(fake, 4, 4, 4, 2, fake, 1, None) == einval         # ldl < r
+    assert lib.pluq_extract_U(fake, 4, 4, 4, 2, fake, 3, None) == einval         # ldu < n
+    assert lib.pluq_leu(fake, 4, 4, 4, 2, fake, fake, None, 4, None, 4, fake, 64,
+                        None) == einval                                           # no output
+    assert lib.pluq_leu(fake, 4, 4, 4, 2, fake, fake, fake, 4, None, 4, fake, 31,
+                        None) == enomem                                           # (m + n) ints
+    assert lib.pluq_leading_rank_profiles(fake, fake, 4, 4, 2, 5, 1, fake, fake, fake,
+                                          None) == einval                         # k > m
+    # kernel-level calls
+    assert lib.pluq_modmm(fake, 4, fake, 4, fake, 4, -1, 4, 4, 65521, 0, 0, fake, 0,
+                          None) == einval
+    assert lib.pluq_modmm(fake, 4, fake, 4, fake, 4, 4, 4, 4, 65521, 0, 5, fake, 0,
+                          None) == einval                                         # form
+    assert lib.pluq_modmm(fake, 4, fake, 4, fake, 4, 4, 4, 4, 15, 0, 0, fake, 0,
+                          None) == enotprime
+    assert lib.pluq_modmm(fake, 3, fake, 4, fake, 4, 4, 4, 4, 65521, 0, 0, fake, 0,
+                          None) == einval                                         # ldc < N
+    assert lib.pluq_trsm_left_lower_unit(fake, 4, fake, 4, 4, 4, 65521, 0, fake, 0,
+                                         None) == enomem
+    assert lib.pluq_trsm_left_lower_unit(fake, 3, fake, 4, 4, 4, 65521, 0, fake, 1 << 30,
+                                         None) == einval                          # ldl < r
+    assert lib.pluq_trsm_right_upper(fake, 4, fake, 4, 4, 4, 4, 0, fake, 1 << 30,
+                                     None) == enotprime
+    assert lib.pluq_perm_rows(fake, 4, -1, 4, fake, fake, 64, None) == einval
+    assert lib.pluq_perm_rows(fake, 4, 0, 4, None, None, 0, None) == ok           # nothing moves
+    assert lib.pluq_perm_rows(fake, 4, 4, 4, fake, fake, 63, None) == enomem
+    assert lib.pluq_perm_cols(fake, 3, 4, 4, fake, fake, 1 << 20, None) == einval  # ldx < count
+    assert lib.pluq_leaf(fake, 129, 4, 4, 65521, fake, fake, fake, None) == einval  # > base case
+    assert lib.pluq_leaf(fake, 4, 4, 4, 65535, fake, fake, fake, None) == enotprime
+    # process-wide knobs: accepted values round-trip, others are refused
+    lf, sm = ctypes.c_int64(0), ctypes.c_int64(0)
+    assert lib.pluq_get_tuning(ctypes.byref(lf), ctypes.byref(sm)) == ok
+    assert lib.pluq_set_tuning(8, 0) == einval and lib.pluq_set_tuning(256, 0) == einval
+    assert lib.pluq_set_tuning(64, 1 << 20) == ok
+    l2, s2 = ctypes.c_int64(0), ctypes.c_int64(0)
+    assert lib.pluq_get_tuning(ctypes.byref(l2), ctypes.byref(s2)) == ok and (l2.value, s2.value) == (64, 1 << 20)
+    assert lib.pluq_set_tuning(lf.value, sm.value) == ok
+    assert lib.pluq_set_node_cluster(3) == einval and lib.pluq_set_node_kernel(3) == einval
+    assert lib.pluq_set_leaf_variant(2) == einval and lib.pluq_set_lazy_zero_test(-1) == einval
+    assert lib.pluq_set_branch_min(0) == einval
+    old = lib.pluq_get_node_cluster()
+    assert lib.pluq_set_node_cluster(8) == ok and lib.pluq_get_node_cluster() == 8
+    assert lib.pluq_set_node_cluster(old) == ok
+
+
 def test_persistent_batch_rejects_bad_arguments_on_the_host():
     """The persistent batch entry point and its workspace query check sizes,
     the modulus, the argument arrays and the workspace before any device work
