@@ -126,7 +126,8 @@ pluq_status pluq_mod_p_batched(uint32_t *const *h_dA, const int64_t *h_m, const 
  * Workspace: pluq_batched_persistent_workspace_size(max_m, max_n, ctas),
  * 16-byte aligned; calls that share a workspace must not overlap.
  * Host-checked errors: EINVAL (count < 0, ctas < 0, max_m / max_n out of
- * range, null arrays), ENOTPRIME, ENOMEM (workspace), ECUDA.
+ * range, null arrays, a workspace not 16-byte aligned), ENOTPRIME, ENOMEM
+ * (workspace missing or too small), ECUDA.
  */
 pluq_status pluq_batched_persistent_workspace_size(int64_t max_m, int64_t max_n, int ctas,
                                                    size_t *h_bytes);

@@ -170,7 +170,8 @@ pluq_status pluq_mod_p_batched_persistent(uint32_t *const *d_A, const int64_t *d
     if (!d_A || !d_m || !d_n || !d_lda || !d_perm_p || !d_perm_q || !d_rank) return PLUQ_EINVAL;
     size_t need = 0;
     PLUQ_TRY(pluq_batched_persistent_workspace_size(max_m, max_n, ctas, &need));
-    if (!d_work || ws_bytes < need || ((uintptr_t)d_work & 15)) return PLUQ_ENOMEM;
+    if (!d_work || ws_bytes < need) return PLUQ_ENOMEM;
+    if ((uintptr_t)d_work & 15) return PLUQ_EINVAL;
     const int nb = (int)std::min<int64_t>(batch_ctas(ctas), count);
     cudaStream_t st = (cudaStream_t)stream;
     BatchArgs a{};

@@ -243,6 +243,8 @@ def test_persistent_batch_rejects_bad_arguments_on_the_host():
                None) == einval                                                 # no m array
     assert run(fake, fake, fake, fake, 3, 100, 30, 65521, fake, fake, fake, fake, need - 1, 4,
                None) == enomem
+    assert run(fake, fake, fake, fake, 3, 100, 30, 65521, fake, fake, fake, fake + 4, need, 4,
+               None) == einval                                                 # misaligned
     assert run(fake, fake, fake, fake, 0, 100, 30, 65521, fake, fake, fake, None, 0, 4,
                None) == ok                                                     # empty batch
 
