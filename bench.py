@@ -241,7 +241,7 @@ def cpu_oracle_rate(target_s: float = 12.0, p: int = 65521):
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("mm_tc.cu", "common.cuh", "leaf_impl.cuh", "leaf.cu", "node_impl.cuh", "node.cu",
-              "batch.cu", "perm.cu"):
+              "perm.cu"):
         with open(os.path.join(ROOT, "paper_1301_4438_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
